@@ -1,0 +1,120 @@
+"""Pins of the oracle's row reduction, y-solve, Algorithm 1 and certificate — CPU only.
+
+The whole-solve pins compare the relaxation optimum p*_kappa with a brute-force
+search of the nonconvex problem (Theorem 1: p*_kappa <= p*, with equality when
+every moment matrix has rank one) on horizons 2 and 3.
+"""
+import numpy as np
+import pytest
+import scipy.optimize as so
+
+import workloads as wl
+from oracle import certify as CE
+from oracle import relax as R
+from oracle import sgs_admm as O
+
+from test_oracle_relax import _pend_rollout, _toy_rollout
+
+
+def test_reduction_rank_and_spd():
+    for p in (wl.toy_problem(N=3), wl.pendulum_problem(N=3, theta0=0.1)):
+        sdp = R.relax(p)
+        keep, _ = O.reduce_rows(sdp)
+        Ad = sdp.A.toarray()
+        rank = np.linalg.matrix_rank(Ad, tol=1e-9 * np.linalg.norm(Ad, 2))
+        assert keep.sum() == rank
+        Ak = Ad[keep]
+        assert np.min(np.linalg.eigvalsh(Ak @ Ak.T)) > 1e-10
+        # every dropped row lies in the span of the kept rows
+        drop = Ad[~keep]
+        if len(drop):
+            coef = np.linalg.lstsq(Ak.T, drop.T, rcond=None)[0]
+            assert np.max(np.abs(Ak.T @ coef - drop.T)) < 1e-9
+
+
+def test_ysolver_backward_error():
+    p = wl.pendulum_problem(N=4, theta0=0.05)
+    red = O.reduce(R.relax(p))
+    ys = O.YSolver(red.A)
+    r = np.random.default_rng(0).standard_normal(red.m)
+    y = ys(r)
+    assert np.linalg.norm(red.A @ (red.A.T @ y) - r) <= 1e-12 * np.linalg.norm(r) * 1e2
+
+
+def _toy_brute(p):
+    N = p.N
+
+    def cost(u):
+        return p.objective(_toy_rollout(p, np.clip(u, -1, 1)))
+    g = np.linspace(-1, 1, 201)
+    if N == 2:
+        U0, U1 = np.meshgrid(g, g, indexing="ij")
+        vals = np.vectorize(lambda a, b: cost([a, b]))(U0, U1)
+        i = np.unravel_index(np.argmin(vals), vals.shape)
+        u0 = np.array([g[i[0]], g[i[1]]])
+    else:
+        u0 = np.zeros(N)
+        best = np.inf
+        for a in np.linspace(-1, 1, 21):
+            for b in np.linspace(-1, 1, 21):
+                for c in np.linspace(-1, 1, 21):
+                    v = cost([a, b, c])
+                    if v < best:
+                        best, u0 = v, np.array([a, b, c])
+    r = so.minimize(cost, u0, bounds=[(-1, 1)] * N, method="L-BFGS-B", options=dict(ftol=1e-15, gtol=1e-12))
+    return min(r.fun, cost(u0))
+
+
+def _pend_brute(p):
+    N = p.N
+
+    def cost(U):
+        z = _pend_rollout(p, np.clip(U, -1, 1))
+        W = z[2::4]
+        if np.max(np.abs(W)) > 1.0:
+            return np.inf
+        return p.objective(z)
+    g = np.linspace(-1, 1, 201)
+    best, u0 = np.inf, None
+    for a in g:
+        for b in g:
+            v = cost([a, b])
+            if v < best:
+                best, u0 = v, np.array([a, b])
+    r = so.minimize(cost, u0, bounds=[(-1, 1)] * N, method="L-BFGS-B", options=dict(ftol=1e-15, gtol=1e-12))
+    return min(r.fun, best)
+
+
+@pytest.mark.parametrize("case", ["toy2", "toy3", "pend2"])
+def test_relaxation_matches_brute_force(case):
+    if case.startswith("toy"):
+        p = wl.toy_problem(N=int(case[-1]))
+        pbf = _toy_brute(p)
+    else:
+        p = wl.pendulum_problem(N=2, theta0=0.12)
+        pbf = _pend_brute(p)
+    red = O.reduce(R.relax(p))
+    res = O.solve(red, O.Options(tol=1e-9, maxiter=40000))
+    assert res.converged
+    cert = CE.certify(p, red, res.X, res.y)
+    # Theorem 1 (ii): p*_kappa <= p*
+    assert res.pobj <= pbf + 1e-6 * (1 + abs(pbf))
+    # valid lower bound <= p* and xi >= 0 (eq. valid-lowerbound, eq. suboptimality)
+    assert cert.lower_bound <= pbf + 1e-9
+    assert cert.xi >= -1e-12
+    # Theorem 1 (iii): rank one => tight
+    if cert.max_ratio < 1e-5:
+        assert abs(res.pobj - pbf) <= 1e-5 * (1 + abs(pbf))
+        assert cert.feasible
+        assert cert.phat >= pbf - 1e-9 * (1 + abs(pbf))
+
+
+def test_admm_detects_wrong_sign():
+    """A planted mistake (sign of C flipped in Step 2) must break the brute-force pin."""
+    p = wl.toy_problem(N=2)
+    red = O.reduce(R.relax(p))
+    good = O.solve(red, O.Options(tol=1e-8, maxiter=20000))
+    bad_sdp = R.relax(p)
+    bad_sdp.C = -bad_sdp.C
+    bad = O.solve(O.ReducedSDP(bad_sdp, red.keep, red.A, red.b, red.blocks), O.Options(tol=1e-8, maxiter=20000))
+    assert abs(bad.pobj - good.pobj) > 1e-2

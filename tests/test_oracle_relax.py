@@ -1,0 +1,214 @@
+"""Pins of the oracle's relaxation builder (Prop. 1, Sec. 2.3) — CPU only."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import relax as R
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "toy_identities.txt")
+DT = 0.1
+
+
+def _golden():
+    out = []
+    for line in open(GOLDEN):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        kind, body, cite = [t.strip() for t in line.split("|")]
+        out.append((kind, body.split(), cite))
+    return out
+
+
+@pytest.fixture(scope="module")
+def toy():
+    p = wl.toy_problem(N=3, dt=DT)
+    return p, R.relax(p)
+
+
+def _entry(sdp, name, i, j):
+    """Global svec index and scale of 1-based entry (i, j) of block name (M2, M3, L21)."""
+    if name[0] == "M":
+        blk = [b for b in sdp.blocks if b.kind == "M"][int(name[1]) - 1]
+    else:
+        blk = [b for b in sdp.blocks if b.kind == "L" and b.clique == int(name[1]) - 1][int(name[2]) - 1]
+    return blk.offset + R.svec_index(i - 1, j - 1), R.svec_scale(i - 1, j - 1)
+
+
+def _row_as_entries(sdp, r):
+    """Row r as {svec index: coefficient on the matrix ENTRY} (svec coef / entry scale)."""
+    A = sdp.A
+    cols = A.indices[A.indptr[r]:A.indptr[r + 1]]
+    vals = A.data[A.indptr[r]:A.indptr[r + 1]]
+    out = {}
+    for c, v in zip(cols, vals):
+        # find the entry scale of column c
+        blk = max((b for b in sdp.blocks if b.offset <= c), key=lambda b: b.offset)
+        p = c - blk.offset
+        j = int((math.isqrt(8 * p + 1) - 1) // 2)
+        i = p - j * (j + 1) // 2
+        out[int(c)] = v / R.svec_scale(i, j)
+    return out
+
+
+def _find_row(sdp, target):
+    """Index of a row proportional to target {svec index: entry coef}, else None."""
+    keys = set(target)
+    for r in range(sdp.m):
+        e = _row_as_entries(sdp, r)
+        if set(e) != keys:
+            continue
+        k0 = next(iter(keys))
+        lam = e[k0] / target[k0]
+        if all(abs(e[k] - lam * target[k]) <= 1e-14 * max(1.0, abs(lam * target[k])) for k in keys):
+            return r
+    return None
+
+
+def _parse_coef(s):
+    return eval(s, {"dt": DT})
+
+
+def test_basis_matches_printed(toy):
+    _, sdp = toy
+    (kind, body, _), = [g for g in _golden() if g[0] == "basis"]
+    names = ["x1", "u1", "x2"]
+    got = []
+    for e in R.monomial_basis(3, 2):
+        s = "".join(n + ("^2" if k == 2 else "") for n, k in zip(names, e) if k)
+        got.append(s or "1")
+    assert got == body
+
+
+def test_mom_identity(toy):
+    _, sdp = toy
+    for kind, body, cite in _golden():
+        if kind != "mom":
+            continue
+        ents = [b.split(":") for b in body]
+        ids = [_entry(sdp, n, *map(int, ij.split(","))) for n, ij in ents]
+        # all of them hold the same monomial: each non-representative is tied to one representative
+        mi = sdp.mindex
+        monos = {tuple(a + b for a, b in zip(mi.basis[int(ij.split(',')[0]) - 1], mi.basis[int(ij.split(',')[1]) - 1]))
+                 for _, ij in ents}
+        assert len(monos) == 1, cite
+        rep = mi.rep[monos.pop()]
+        p_rep, _ = _entry(sdp, ents[0][0], rep[0] + 1, rep[1] + 1)
+        for (p, s) in ids:
+            if p == p_rep:
+                continue
+            assert _find_row(sdp, {p: 1.0, p_rep: -1.0}) is not None, cite
+
+
+@pytest.mark.parametrize("kind", ["ineq", "eq"])
+def test_linear_identities(toy, kind):
+    _, sdp = toy
+    for k, body, cite in _golden():
+        if k != kind:
+            continue
+        tgt = {}
+        for t in body:
+            name, ij, c = t.split(":")
+            p, _ = _entry(sdp, name, *map(int, ij.split(",")))
+            tgt[p] = tgt.get(p, 0.0) + _parse_coef(c)
+        assert _find_row(sdp, tgt) is not None, cite
+
+
+def test_eq_count(toy):
+    _, sdp = toy
+    (_, body, cite), = [g for g in _golden() if g[0] == "eqcount"]
+    # clique 2 has one equality h_{2,1} of degree 2 -> s(3, 2) rows
+    n_eq = int(np.sum((sdp.row_kind == R.KIND_EQ) & (sdp.row_clique == 1)))
+    assert n_eq == int(body[0]), cite
+
+
+def test_consensus(toy):
+    _, sdp = toy
+    for kind, body, cite in _golden():
+        if kind != "cons":
+            continue
+        (n1, ij1), (n2, ij2) = [b.split(":") for b in body]
+        p1, _ = _entry(sdp, n1, *map(int, ij1.split(",")))
+        p2, _ = _entry(sdp, n2, *map(int, ij2.split(",")))
+        if ij1 == "1,1":
+            # the constant monomial: both equal 1 through their phi_0 rows
+            for p in (p1, p2):
+                r = _find_row(sdp, {p: 1.0})
+                assert r is not None and sdp.b[r] == 1.0, cite
+        else:
+            assert _find_row(sdp, {p1: 1.0, p2: -1.0}) is not None, cite
+
+
+def test_table1_sizes():
+    (_, body, cite), = [g for g in _golden() if g[0] == "sizes"]
+    for t in body:
+        nv, sM, sL = map(int, t.split(":"))
+        assert len(R.monomial_basis(nv, 2)) == sM == R.s_count(nv, 2), cite
+        assert len(R.monomial_basis(nv, 1)) == sL == R.s_count(nv, 1), cite
+
+
+# --------------------------------------------------------------------------
+# rank-1 lifting of a feasible point satisfies A(X(z)) = b and <C, X(z)> = sum f_k
+# (eq. rank1-lifting and the identity chain of eq. inexact-lower-bound)
+# --------------------------------------------------------------------------
+def _toy_rollout(p, u):
+    dt, x = p.meta["dt"], [p.meta["x_init"]]
+    z = [x[0]]
+    for uk in u:
+        xn = z[-1] - dt * (1.0 + uk) * z[-1]
+        z += [uk, xn]
+    return np.array(z)
+
+
+def _pend_rollout(p, U):
+    """Explicit pendulum simulation in the rescaled variables (Cayley rotation, 2x2 solve)."""
+    m = p.meta
+    dt, wmax, umax, gl = m["dt"], m["w_max"], m["u_max"], m["g_l"]
+    c, s, W = np.cos(m["theta0"]), np.sin(m["theta0"]), 0.0
+    z = [c, s, W]
+    h = 0.5 * dt * wmax
+    for Uk in U:
+        a = h * W
+        # [1 a; -a 1] [c+; s+] = [c - a s; s + a c]
+        rhs1, rhs2 = c - a * s, s + a * c
+        det = 1.0 + a * a
+        cn, sn = (rhs1 - a * rhs2) / det, (rhs2 + a * rhs1) / det
+        Wn = W + dt / wmax * (umax * Uk - gl * s)
+        z += [Uk, cn, sn, Wn]
+        c, s, W = cn, sn, Wn
+    return np.array(z)
+
+
+@pytest.mark.parametrize("which", ["toy", "pendulum"])
+def test_lifting_feasible(which):
+    rng = np.random.default_rng(3)
+    if which == "toy":
+        p = wl.toy_problem(N=4, dt=DT)
+        z = _toy_rollout(p, rng.uniform(-1, 1, 4))
+    else:
+        p = wl.pendulum_problem(N=4, theta0=0.15)
+        z = _pend_rollout(p, rng.uniform(-1, 1, 4))
+    sdp = R.relax(p)
+    X = R.lift_rank1(p, sdp, z)
+    res = sdp.A @ X - sdp.b
+    assert np.max(np.abs(res)) < 1e-12
+    assert abs(sdp.C @ X - p.objective(z)) < 1e-12 * (1 + abs(p.objective(z)))
+
+
+def test_lifting_detects_infeasible():
+    p = wl.pendulum_problem(N=3, theta0=0.15)
+    z = _pend_rollout(p, [0.3, -0.2, 0.5])
+    z[5] += 1e-3               # break the dynamics of one state
+    sdp = R.relax(p)
+    assert np.max(np.abs(sdp.A @ R.lift_rank1(p, sdp, z) - sdp.b)) > 1e-5
+
+
+def test_pendulum_shapes():
+    p = wl.pendulum_problem(N=10)
+    sdp = R.relax(p)
+    sizes = [b.n for b in sdp.blocks]
+    assert sizes.count(36) == 10 and sizes.count(8) == 20
+    assert sdp.nsvec == 10 * 666 + 20 * 36

@@ -1,0 +1,16 @@
+"""Seeded synthetic inputs shared by the oracle, the tests and the bench.
+
+This package builds *problem data only*: the polynomial trajectory problems
+(objective, inequality and equality polynomials per clique, Definition 1 /
+eq. (1)) and the random symmetric matrices of the PSD-projection microbench.
+It contains none of the relaxation, ADMM or projection arithmetic; both the
+oracle and the CUDA path read what it produces.
+"""
+from .poly import Poly
+from .problems import (Problem, Clique, toy_problem, pendulum_problem,
+                       cartpole_problem, rigid_body_problem, problem_batch)
+from .psd_bench import psd_microbench, known_spectrum_blocks
+
+__all__ = ["Poly", "Problem", "Clique", "toy_problem", "pendulum_problem",
+           "cartpole_problem", "rigid_body_problem", "problem_batch",
+           "psd_microbench", "known_spectrum_blocks"]

@@ -1,0 +1,259 @@
+"""Polynomial trajectory problems with chain-like sparsity (Definition 1).
+
+Every problem is a list of N cliques. Clique k (1-based, k = 1..N) holds the
+variables z(I_k) = (x_{k-1}, u_{k-1}, x_k) in that order (Sec. 2.1), so the
+overlap of cliques k and k+1 is x_k: the last dx variables of clique k and
+the first dx variables of clique k+1. For each clique the data are the
+objective term f_k, the inequality polynomials g_{k,i} >= 0 and the equality
+polynomials h_{k,j} = 0, all in clique-local variables.
+
+Variables are rescaled to [-1, 1] by their bounds and every constraint
+polynomial is divided by its largest |coefficient| (Sec. 5, general setup);
+the objective is divided by one global constant. The rotation (cos, sin)
+pairs are propagated with the implicit-midpoint (Cayley) rotation
+  c+ + h w s+ = c - h w s,   s+ - h w c+ = s + h w c,   h = dt/2,
+which is polynomial of degree 2 and keeps c^2 + s^2 fixed exactly, so the
+per-step circle equality c^2 + s^2 = 1 is consistent with the dynamics.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .poly import Poly
+
+
+@dataclass
+class Clique:
+    f: Poly
+    g: list
+    h: list
+
+
+@dataclass
+class Problem:
+    name: str
+    N: int
+    dx: int
+    du: int
+    cliques: list
+    R: float = 1.0                 # bound on |z_i| after rescaling (Theorem 1)
+    kappa: int = 2
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def nv(self) -> int:
+        return 2 * self.dx + self.du
+
+    def clique_arrays(self, k: int):
+        """Clique k (0-based) as ((coef, expo) of f, [g...], [h...])."""
+        c = self.cliques[k]
+        return c.f.arrays(), [p.arrays() for p in c.g], [p.arrays() for p in c.h]
+
+    def objective(self, z) -> float:
+        """Sum_k f_k(z(I_k)) for a global vector z = (x0, u0, x1, u1, ..., xN)."""
+        return sum(c.f.evaluate(self.clique_vars(z, k)) for k, c in enumerate(self.cliques))
+
+    def clique_vars(self, z, k: int):
+        s = k * (self.dx + self.du)
+        return np.asarray(z, dtype=np.float64)[s:s + self.nv]
+
+    @property
+    def nz(self) -> int:
+        return self.N * (self.dx + self.du) + self.dx
+
+
+# --------------------------------------------------------------------------
+# toy 1-D system of Example 1 (unscaled, exactly as printed)
+# --------------------------------------------------------------------------
+def toy_problem(N: int = 3, dt: float = 0.1, Pf: float = 1.0, x_init: float = 2.0) -> Problem:
+    """Example 1: x_k = x_{k-1} - dt (1 + u_{k-1}) x_{k-1}, |u| <= 1, x_0 = x_init.
+
+    Clique data follow eq. (toy-as-sparse-pop): f_k = u^2 + x_{k-1}^2 plus
+    Pf x_N^2 in the last clique, g = 1 - u^2, h_1 = x_k + (dt-1) x_{k-1} +
+    dt u x_{k-1}, and h_2 = x_0 - x_init in clique 1 only.
+    """
+    nv = 3
+    X0, U, X1 = (Poly.var(nv, i) for i in range(3))
+    cl = []
+    for k in range(1, N + 1):
+        f = U * U + X0 * X0
+        if k == N:
+            f = f + Pf * X1 * X1
+        g = [1.0 - U * U]
+        h = [X1 + (dt - 1.0) * X0 + dt * U * X0]
+        if k == 1:
+            h.append(X0 - x_init)
+        cl.append(Clique(f, g, h))
+    return Problem("toy", N, 1, 1, cl, R=max(1.0, abs(x_init)),
+                   meta=dict(dt=dt, Pf=Pf, x_init=x_init))
+
+
+def _cayley(c0, s0, w, c1, s1, hw):
+    """Implicit-midpoint rotation by angle ~ 2*atan(hw*w), as two equalities."""
+    e1 = c1 + hw * w * s1 - c0 + hw * w * s0
+    e2 = s1 - hw * w * c1 - s0 - hw * w * c0
+    return e1, e2
+
+
+# --------------------------------------------------------------------------
+# pendulum swing-up: state (c, s, w), control u
+# --------------------------------------------------------------------------
+def pendulum_problem(N: int = 10, dt: float = 0.1, theta0: float = 0.1, g_l: float = 9.81,
+                     u_max: float = 2.0, w_max: float = 4.0) -> Problem:
+    """Pendulum: theta from hanging, c = cos(theta), s = sin(theta), w = theta-dot.
+
+    Rescaled variables: w = w_max * W, u = u_max * U.
+      rotation : Cayley step with w_{k-1}
+      rate     : w_k = w_{k-1} + dt (u_{k-1} - g/l s_{k-1})
+      circle   : c_k^2 + s_k^2 = 1
+      bounds   : 1 - U^2 >= 0, 1 - W_k^2 >= 0
+      cost     : sum_{k=0}^{N-1} 10 (1 + c_k)^2 + w_k^2 + 0.1 u_k^2
+                 + 10 (1 + c_N)^2 + w_N^2     (terminal weight Pf = 1)
+      initial  : c_0 = cos(theta0), s_0 = sin(theta0), w_0 = 0 (clique 1)
+    """
+    nv = 7
+    C0, S0, W0, U, C1, S1, W1 = (Poly.var(nv, i) for i in range(nv))
+    hw = 0.5 * dt * w_max
+    raw = []
+    for k in range(1, N + 1):
+        f = 10.0 * (1.0 + C0) ** 2 + (w_max ** 2) * W0 * W0 + 0.1 * (u_max ** 2) * U * U
+        if k == N:
+            f = f + 10.0 * (1.0 + C1) ** 2 + (w_max ** 2) * W1 * W1
+        e1, e2 = _cayley(C0, S0, W0, C1, S1, hw)
+        e3 = W1 - W0 - (dt / w_max) * (u_max * U - g_l * S0)
+        e4 = C1 * C1 + S1 * S1 - 1.0
+        h = [e1, e2, e3, e4]
+        if k == 1:
+            h += [C0 - np.cos(theta0), S0 - np.sin(theta0), W0 - 0.0]
+        g = [1.0 - U * U, 1.0 - W1 * W1]
+        raw.append((f, g, h))
+    fscale = 1.0 / max(f.max_abs_coef() for f, _, _ in raw)
+    cl = [Clique(f * fscale, [p.normalized() for p in g], [p.normalized() for p in h])
+          for f, g, h in raw]
+    return Problem("pendulum", N, 3, 1, cl, R=1.0,
+                   meta=dict(dt=dt, theta0=theta0, g_l=g_l, u_max=u_max, w_max=w_max,
+                             fscale=fscale, x_init=[np.cos(theta0), np.sin(theta0), 0.0]))
+
+
+# --------------------------------------------------------------------------
+# cart-pole swing-up: state (x, v, c, s, w), control force f
+# --------------------------------------------------------------------------
+def cartpole_problem(N: int = 50, dt: float = 0.05, x0: float = 0.0, theta0: float = 0.0,
+                     mc: float = 1.0, mp: float = 0.1, l: float = 0.5, g: float = 9.81,
+                     f_max: float = 10.0, x_max: float = 2.0, v_max: float = 4.0,
+                     w_max: float = 10.0) -> Problem:
+    """Cart-pole, theta from hanging, dynamics multiplied by D = mc + mp s^2.
+
+      x_k = x_{k-1} + dt v_{k-1}
+      D (v_k - v_{k-1}) = dt (f + mp s (g c + l w^2))
+      l D (w_k - w_{k-1}) = dt (-c f - mp l c s w^2 - (mc + mp) g s)
+      (c, s) Cayley step with w_{k-1};  c_k^2 + s_k^2 = 1
+      boxes on f, x_k, v_k, w_k;  LQR-style cost towards (0, 0, -1, 0, 0).
+    """
+    nv = 11
+    V = [Poly.var(nv, i) for i in range(nv)]
+    X0, V0, C0, S0, W0, F, X1, V1, C1, S1, W1 = V
+    hw = 0.5 * dt * w_max
+    D = mc + mp * S0 * S0
+    raw = []
+    for k in range(1, N + 1):
+        stage = (X0 * X0 + V0 * V0 + (C0 + 1.0) ** 2 + S0 * S0 + W0 * W0 + F * F)
+        if k == N:
+            stage = stage + X1 * X1 + V1 * V1 + (C1 + 1.0) ** 2 + S1 * S1 + W1 * W1
+        e_x = x_max * X1 - x_max * X0 - dt * v_max * V0
+        e_v = D * (v_max * V1 - v_max * V0) - dt * (f_max * F + mp * S0 * (g * C0 + l * w_max ** 2 * W0 * W0))
+        e_w = l * D * (w_max * W1 - w_max * W0) - dt * (-f_max * C0 * F - mp * l * w_max ** 2 * C0 * S0 * W0 * W0
+                                                       - (mc + mp) * g * S0)
+        e1, e2 = _cayley(C0, S0, W0, C1, S1, hw)
+        e_c = C1 * C1 + S1 * S1 - 1.0
+        h = [e_x, e_v, e_w, e1, e2, e_c]
+        if k == 1:
+            h += [X0 - x0 / x_max, V0 - 0.0, C0 - np.cos(theta0), S0 - np.sin(theta0), W0 - 0.0]
+        gg = [1.0 - F * F, 1.0 - X1 * X1, 1.0 - V1 * V1, 1.0 - W1 * W1]
+        raw.append((stage, gg, h))
+    fscale = 1.0 / max(f.max_abs_coef() for f, _, _ in raw)
+    cl = [Clique(f * fscale, [p.normalized() for p in gg], [p.normalized() for p in h])
+          for f, gg, h in raw]
+    return Problem("cartpole", N, 5, 1, cl, R=1.0,
+                   meta=dict(dt=dt, x0=x0, theta0=theta0, fscale=fscale,
+                             x_init=[x0 / x_max, 0.0, np.cos(theta0), np.sin(theta0), 0.0]))
+
+
+# --------------------------------------------------------------------------
+# planar rigid body among disk obstacles: state (rx, ry, c, s, vx, vy, w),
+# control (fc, fs) with fc^2 + fs^2 <= 1 (body-frame force)
+# --------------------------------------------------------------------------
+def rigid_body_problem(N: int = 20, dt: float = 0.1, start=(-0.8, -0.8, 0.0), goal=(0.5, 0.5, 0.0),
+                       disks=(), p_max: float = 2.5, v_max: float = 2.0, w_max: float = 2.0,
+                       a_max: float = 1.0, lever: float = 0.5) -> Problem:
+    nv = 16
+    V = [Poly.var(nv, i) for i in range(nv)]
+    RX0, RY0, C0, S0, VX0, VY0, W0, FC, FS, RX1, RY1, C1, S1, VX1, VY1, W1 = V
+    hw = 0.5 * dt * w_max
+    gx, gy, gth = goal
+    gxs, gys = gx / p_max, gy / p_max
+    raw = []
+    for k in range(1, N + 1):
+        stage = ((RX0 - gxs) ** 2 + (RY0 - gys) ** 2 + (C0 - np.cos(gth)) ** 2 + (S0 - np.sin(gth)) ** 2
+                 + VX0 * VX0 + VY0 * VY0 + W0 * W0 + FC * FC + FS * FS)
+        if k == N:
+            stage = stage + ((RX1 - gxs) ** 2 + (RY1 - gys) ** 2 + (C1 - np.cos(gth)) ** 2
+                             + (S1 - np.sin(gth)) ** 2 + VX1 * VX1 + VY1 * VY1 + W1 * W1)
+        s = dt * v_max / p_max
+        e_rx = RX1 - RX0 - s * VX0
+        e_ry = RY1 - RY0 - s * VY0
+        a = dt * a_max / v_max
+        e_vx = VX1 - VX0 - a * (C0 * FC - S0 * FS)
+        e_vy = VY1 - VY0 - a * (S0 * FC + C0 * FS)
+        e_w = W1 - W0 - (dt * a_max * lever / w_max) * FS
+        e1, e2 = _cayley(C0, S0, W0, C1, S1, hw)
+        e_c = C1 * C1 + S1 * S1 - 1.0
+        h = [e_rx, e_ry, e_vx, e_vy, e_w, e1, e2, e_c]
+        if k == 1:
+            sx, sy, sth = start
+            h += [RX0 - sx / p_max, RY0 - sy / p_max, C0 - np.cos(sth), S0 - np.sin(sth),
+                  VX0 - 0.0, VY0 - 0.0, W0 - 0.0]
+        gg = [1.0 - FC * FC - FS * FS, 1.0 - VX1 * VX1, 1.0 - VY1 * VY1, 1.0 - W1 * W1]
+        for (ox, oy, rho) in disks:
+            gg.append((RX1 - ox / p_max) ** 2 + (RY1 - oy / p_max) ** 2 - (rho / p_max) ** 2)
+        raw.append((stage, gg, h))
+    fscale = 1.0 / max(f.max_abs_coef() for f, _, _ in raw)
+    cl = [Clique(f * fscale, [p.normalized() for p in gg], [p.normalized() for p in h])
+          for f, gg, h in raw]
+    return Problem("rigid_body", N, 7, 2, cl, R=1.0,
+                   meta=dict(dt=dt, start=start, goal=goal, disks=list(disks), fscale=fscale))
+
+
+# --------------------------------------------------------------------------
+# seeded batches (base seed 20240607, instance i uses seed + i)
+# --------------------------------------------------------------------------
+BASE_SEED = 20240607
+
+
+def problem_batch(kind: str, B: int, seed: int = BASE_SEED, **kw):
+    out = []
+    for i in range(B):
+        rng = np.random.default_rng(np.random.PCG64(seed + i))
+        if kind == "pendulum":
+            out.append(pendulum_problem(theta0=float(rng.uniform(-0.2, 0.2)), **kw))
+        elif kind == "cartpole":
+            out.append(cartpole_problem(x0=float(rng.uniform(-0.5, 0.5)),
+                                        theta0=float(rng.uniform(-0.3, 0.3)), **kw))
+        elif kind == "rigid_body":
+            N = kw.pop("N", None) or int(rng.integers(20, 101))
+            nd = int(rng.integers(2, 5))
+            start = (-1.5, -1.5, 0.0)
+            goal = (float(rng.uniform(-1, 1)), float(rng.uniform(-1, 1)), float(rng.uniform(-np.pi, np.pi)))
+            disks = []
+            while len(disks) < nd:
+                ox, oy = rng.uniform(-2, 2, size=2)
+                rho = rng.uniform(0.3, 1.0)
+                if (np.hypot(ox - start[0], oy - start[1]) > rho + 0.2
+                        and np.hypot(ox - goal[0], oy - goal[1]) > rho + 0.2):
+                    disks.append((float(ox), float(oy), float(rho)))
+            out.append(rigid_body_problem(N=N, start=start, goal=goal, disks=disks, **kw))
+        else:
+            raise ValueError(kind)
+    return out
