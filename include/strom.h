@@ -1,0 +1,233 @@
+/* strom.h — C ABI of the GB300-native STROM solver (sparse moment relaxation +
+ * sGS-ADMM) of "Fast and Certifiable Trajectory Optimization" (Kang et al.).
+ *
+ * Conventions
+ *   - Every call returns an int status (STROM_OK = 0, negative = error); the
+ *     message of the last error on the calling thread is strom_last_error().
+ *   - Opaque handles are created by *_create and freed by *_destroy; the
+ *     caller owns them. Input arrays are borrowed for the duration of the call
+ *     and copied; output arrays are caller-allocated with sizes from *_info.
+ *   - Pointers named *_dev are CUDA device pointers on the current device;
+ *     all other pointers are host pointers. `stream` is a cudaStream_t passed
+ *     as void* (NULL = legacy default stream).
+ *   - svec is the SDPT3 vectorisation: column-major upper triangle, off-diagonal
+ *     entries multiplied by sqrt(2), so <A, B> = svec(A) . svec(B) (Sec. 4).
+ *   - No C++ exception crosses this interface.
+ */
+#ifndef STROM_H
+#define STROM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  STROM_OK = 0,
+  STROM_MAXITER = 1,          /* results valid, tolerance not reached */
+  STROM_ERR_INVALID = -1,     /* bad argument or malformed problem */
+  STROM_ERR_OOM = -2,         /* device or host allocation failed */
+  STROM_ERR_NOT_PD = -3,      /* A A^T not positive definite after row reduction */
+  STROM_ERR_NUMERICAL = -4,   /* NaN / Inf met */
+  STROM_ERR_TIMEOUT = -5,     /* time budget exhausted */
+  STROM_ERR_CUDA = -6         /* a CUDA runtime call failed */
+};
+
+/* precision modes of the PSD projection */
+enum {
+  STROM_PREC_FP64 = 0,        /* Jacobi eigensolver in FP64 (plain) */
+  STROM_PREC_FP32 = 1,        /* Jacobi eigensolver in FP32 */
+  STROM_PREC_MIXED = 2        /* FP32 Jacobi, FP64 polish once eta <= polish_eta */
+};
+
+const char* strom_last_error(void);
+const char* strom_version(void);
+
+/* ------------------------------------------------------------------------
+ * Problem: a polynomial optimization problem with chain-like sparsity
+ * (Definition 1, eq. chain-sparse-pop) describing a trajectory problem
+ * (eq. intro:trajopt). Clique k (0-based, k < N) has the n_v = 2 dx + du
+ * variables z(I_k) = (x_{k-1}, u_{k-1}, x_k) (Sec. 2.1); consecutive cliques
+ * overlap in x_k. Polynomials use clique-local exponents.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  int32_t nterms;
+  const double* coef;        /* [nterms] */
+  const uint8_t* expo;       /* [nterms * n_v], row-major: term t has expo[t*n_v + i] */
+} strom_poly;
+
+typedef struct {
+  strom_poly f;              /* objective term f_k */
+  int32_t ng;                /* inequalities g_{k,i} >= 0, degree 1 or 2 (Sec. 4 assumption iii) */
+  const strom_poly* g;
+  int32_t nh;                /* equalities h_{k,j} = 0, degree <= 2 kappa */
+  const strom_poly* h;
+} strom_clique;
+
+typedef struct {
+  int32_t N, dx, du;
+  int32_t kappa;             /* relaxation order; must be 2 (Sec. 4 assumption i) */
+  double R;                  /* bound |z_i| <= R on every variable (Theorem 1) */
+  const strom_clique* cliques;   /* [N] */
+} strom_problem_desc;
+
+typedef struct strom_problem strom_problem;
+
+/* Copies the description. Errors: INVALID (kappa != 2, a degree out of range,
+ * an exponent tuple of the wrong length, N < 1). */
+int strom_problem_create(const strom_problem_desc* desc, strom_problem** out);
+void strom_problem_destroy(strom_problem* p);
+
+/* ------------------------------------------------------------------------
+ * Relaxation: the order-2 sparse moment relaxation (Prop. 1) written as the
+ * PSD-only standard SDP  min <C,X> s.t. A(X) = b, X in Omega_+
+ * (eq. standardsdp, Sec. 2.3). Blocks are ordered M_1, L_{1,1..}, M_2, ...;
+ * rows are ordered by clique and inside a clique as A_mom, A_ineq, A_eq, the
+ * phi_0 = 1 row, then the consensus rows A_sen with clique k+1. A monomial
+ * of M_k is represented by its first occurrence in column-major upper order.
+ * ---------------------------------------------------------------------- */
+typedef struct strom_sdp strom_sdp;
+
+typedef struct {
+  int32_t N, nv, nblocks;
+  int64_t nsvec;             /* length of svec(X) */
+  int64_t m;                 /* rows of A (before row reduction) */
+  int64_t nnz;               /* nonzeros of A */
+  int64_t rows_by_kind[5];   /* A_mom, A_ineq, A_eq, phi_0, A_sen */
+} strom_sdp_info;
+
+enum { STROM_ROW_MOM = 0, STROM_ROW_INEQ = 1, STROM_ROW_EQ = 2, STROM_ROW_PHI0 = 3, STROM_ROW_CONS = 4 };
+
+int strom_relax(const strom_problem* p, strom_sdp** out);
+int strom_sdp_info_get(const strom_sdp* s, strom_sdp_info* info);
+/* Any output pointer may be NULL to skip it. Sizes: block_* [nblocks],
+ * C [nsvec], rowptr [m+1], col/val [nnz] (CSR, columns sorted), b/row_kind/
+ * row_clique [m]. block_kind: 0 = moment, 1 = localizing. */
+int strom_sdp_export(const strom_sdp* s, int32_t* block_n, int64_t* block_off, int8_t* block_kind,
+                     int32_t* block_clique, double* C, int64_t* rowptr, int32_t* col, double* val,
+                     double* b, int8_t* row_kind, int32_t* row_clique);
+void strom_sdp_destroy(strom_sdp* s);
+
+/* ------------------------------------------------------------------------
+ * Solver: sGS-ADMM (Algorithm 1) on a batch of independent SDPs, all on the
+ * current CUDA device. Creation uploads the data, removes linearly dependent
+ * rows (pivot-skipping Cholesky of A A^T in the order cliques N..1, natural
+ * row order inside a clique; a row is dropped when its pivot is at most
+ * rank_tol times its squared norm) and factorises A A^T once (Sec. 4, hybrid
+ * linear system solver; here entirely on the GPU).
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  double tol;                /* stop when max(eta_p, eta_d, eta_g) <= tol (eq. kkt-residual) */
+  int32_t maxiter;
+  double sigma0, tau;        /* Algorithm 1 inputs: sigma > 0, tau in (0, 2) */
+  int32_t sigma_every;       /* sigma update cadence (iterations) */
+  double sigma_ratio, sigma_factor, sigma_min, sigma_max;
+  double rank_tol;           /* relative pivot threshold of the row reduction */
+  int32_t precision;         /* STROM_PREC_* */
+  double polish_eta;         /* MIXED: switch to the FP64 eigensolver once eta <= polish_eta */
+  int32_t check_every;       /* host checks for completion every this many iterations */
+  double time_budget_s;      /* <= 0: none */
+} strom_options;
+
+void strom_options_default(strom_options* o);
+
+typedef struct strom_solver strom_solver;
+
+typedef struct {
+  int32_t status;            /* STROM_OK, STROM_MAXITER or an error */
+  int32_t iterations;
+  double pobj, dobj;         /* <C, X>, <b, y> */
+  double eta_p, eta_d, eta_g;
+  double sigma;
+  int64_t m_kept;            /* rows kept by the row reduction */
+} strom_result;
+
+/* sdps: [count] relaxations (each may be different). Errors: INVALID, OOM,
+ * NOT_PD (a pivot of a kept row became non-positive), CUDA. */
+int strom_solver_create(const strom_sdp* const* sdps, int32_t count, const strom_options* opt,
+                        strom_solver** out);
+void strom_solver_destroy(strom_solver* s);
+int32_t strom_solver_count(const strom_solver* s);
+
+/* Runs Algorithm 1 until every instance meets tol or maxiter. Returns
+ * STROM_OK when all converged, STROM_MAXITER otherwise. */
+int strom_solve(strom_solver* s, void* stream);
+/* Runs at most `iters` more iterations (instances that already met tol stay
+ * frozen). *n_active receives the number of unconverged instances. */
+int strom_solver_step(strom_solver* s, int32_t iters, void* stream, int32_t* n_active);
+/* Resets instance i to (X, S, y, sigma) = (X0, S0, 0, sigma) (warm start,
+ * Algorithm 1 input); NULL X0/S0 mean zero, sigma <= 0 means opt.sigma0. */
+int strom_solver_reset(strom_solver* s, int32_t i, const double* X0, const double* S0, double sigma);
+
+int strom_get_result(const strom_solver* s, int32_t i, strom_result* r);
+/* Host copies of the state of instance i: X, S [nsvec], y [m] (dropped rows
+ * hold 0). Any pointer may be NULL. */
+int strom_get_state(const strom_solver* s, int32_t i, double* X, double* S, double* y);
+/* Moment matrix M_k of instance i as a dense column-major n x n matrix. */
+int strom_get_moment(const strom_solver* s, int32_t i, int32_t k, double* Mk);
+/* Row keep-mask of instance i after the row reduction [m]. */
+int strom_get_kept_rows(const strom_solver* s, int32_t i, uint8_t* keep);
+
+/* ------------------------------------------------------------------------
+ * Certificate (end of solve): rank-1 test of every M_k (Theorem 1 iii),
+ * extraction of z_bar from the top eigenvectors (Sec. 2.2), a rollout that
+ * clips the controls to [-R, R] and solves each clique's equalities for its
+ * new state by Gauss-Newton (stands in for the paper's local solver), the
+ * valid lower bound <b,y> + sum_beta R_beta min(0, lambda_min((C - A^T y)_beta))
+ * (eq. valid-lowerbound, R_beta of App. C) and xi (eq. suboptimality-gap).
+ * Eigenvalues are computed on the GPU in FP64.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+  double max_ratio;          /* max_k lambda_2 / lambda_1 of M_k */
+  double lower_bound;
+  double phat;               /* objective at the rolled-out point */
+  double xi;
+  double hmax, gmin;         /* max |h|, min g at the rolled-out point */
+  int32_t feasible, rank_one, certified;
+} strom_certificate;
+
+/* zbar, zhat: optional host outputs of length N (dx + du) + dx. */
+int strom_certify(strom_solver* s, int32_t i, const strom_problem* p, double rank_tol, double xi_tol,
+                  strom_certificate* out, double* zbar, double* zhat);
+
+/* ------------------------------------------------------------------------
+ * Kernel-level entry points for parity tests (device pointers, caller's
+ * stream). They use the solver's uploaded operator of the whole batch: x has
+ * length strom_solver_nsvec_total, y and r have length strom_solver_m_total.
+ * ---------------------------------------------------------------------- */
+int64_t strom_solver_nsvec_total(const strom_solver* s);
+int64_t strom_solver_m_total(const strom_solver* s);
+/* Offsets of instance i inside the batch vectors. */
+int strom_solver_offsets(const strom_solver* s, int32_t i, int64_t* svec_off, int64_t* row_off);
+/* Ax_dev = A(x_dev) = (<A_i, X>)_i (Sec. 3); all rows, dropped ones included. */
+int strom_kernel_A(const strom_solver* s, const double* x_dev, double* Ax_dev, void* stream);
+/* x_dev = A^* y = sum_l y_l A_l over all rows (Sec. 3). */
+int strom_kernel_At(const strom_solver* s, const double* y_dev, double* x_dev, void* stream);
+/* y_dev = (A_K A_K^T)^{-1} r_K on the kept rows K, zero on dropped rows
+ * (eq. solve-y1 / solve-y2). r_dev entries of dropped rows are ignored. */
+int strom_kernel_solve(const strom_solver* s, const double* r_dev, double* y_dev, void* stream);
+
+/* ------------------------------------------------------------------------
+ * PSD projection of a list of symmetric blocks given in svec form
+ * (Sec. 4, parallel PSD cone projection): P = Q max(0, W) Q^T per block.
+ * A plan uploads the block table once; execute may be called many times.
+ * blk_off[i] is the svec offset of block i, blk_n[i] its size (1..160).
+ * ---------------------------------------------------------------------- */
+typedef struct strom_psd_plan strom_psd_plan;
+int strom_psd_plan_create(const int64_t* blk_off, const int32_t* blk_n, int32_t nblk, int32_t precision,
+                          strom_psd_plan** out);
+void strom_psd_plan_destroy(strom_psd_plan* p);
+/* P_dev = Pi(Xb_dev) block by block; Xb_dev and P_dev may not alias.
+ * Optionally lam_dev receives the eigenvalues (ascending) of each block,
+ * packed at offsets sum of previous blk_n (NULL to skip). */
+int strom_psd_execute(strom_psd_plan* p, const double* Xb_dev, double* P_dev, double* lam_dev, void* stream);
+/* One-shot form (creates and destroys a plan). */
+int strom_kernel_psd_project(const double* Xb_dev, const int64_t* blk_off, const int32_t* blk_n,
+                             int32_t nblk, int32_t precision, double* P_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STROM_H */

@@ -16,7 +16,7 @@ Readings of the paper that are ours (the paper leaves them open): the
 penalty sigma is adapted every 20 iterations by halving it when
 max(eta_p, eta_g) > 5 eta_d and doubling it when eta_d > 5 max(eta_p, eta_g)
 (clipped to [1e-4, 1e4]);
-tau = 1.618; X0 = S0 = 0; residuals use (X^{k+1}, y^{k+1}, S^{k+1}) and the
+tau = 1.618; sigma0 = 10; X0 = S0 = 0; residuals use (X^{k+1}, y^{k+1}, S^{k+1}) and the
 row-reduced A.
 """
 from __future__ import annotations
@@ -157,7 +157,7 @@ class YSolver:
 class Options:
     tol: float = 1e-6
     maxiter: int = 50000
-    sigma0: float = 1.0
+    sigma0: float = 10.0
     tau: float = 1.618
     sigma_every: int = 20
     sigma_ratio: float = 5.0

@@ -1,0 +1,264 @@
+"""Thin Python layer over the C ABI: marshalling of problems, SDPs, solvers and plans.
+
+Every computation runs in libstrom (host C++ builder, CUDA kernels); this
+module only converts arrays and keeps them alive across calls. Device
+vectors are passed as raw pointers (e.g. torch tensors' data_ptr()).
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _native as N
+from ._native import check, lib
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+class Problem:
+    """A polynomial trajectory problem handed to the library (strom_problem_create).
+
+    `src` is any object with N, dx, du, kappa, R and cliques[k].f/.g/.h, where
+    each polynomial exposes arrays() -> (coef float64[T], expo uint8[T, n_v]).
+    """
+
+    def __init__(self, src):
+        self._keep = []
+        nv = 2 * src.dx + src.du
+
+        def poly(p):
+            coef, expo = p.arrays() if hasattr(p, "arrays") else p
+            coef = np.ascontiguousarray(coef, dtype=np.float64)
+            expo = np.ascontiguousarray(expo, dtype=np.uint8).reshape(len(coef), nv)
+            self._keep += [coef, expo]
+            return N.strom_poly(len(coef), _ptr(coef, C.c_double), _ptr(expo, C.c_uint8))
+
+        cl = (N.strom_clique * src.N)()
+        for k, c in enumerate(src.cliques):
+            g = (N.strom_poly * max(1, len(c.g)))(*[poly(x) for x in c.g])
+            h = (N.strom_poly * max(1, len(c.h)))(*[poly(x) for x in c.h])
+            self._keep += [g, h]
+            cl[k] = N.strom_clique(poly(c.f), len(c.g), g, len(c.h), h)
+        self._keep.append(cl)
+        desc = N.strom_problem_desc(src.N, src.dx, src.du, getattr(src, "kappa", 2), float(src.R), cl)
+        h = C.c_void_p()
+        check(lib().strom_problem_create(C.byref(desc), C.byref(h)), "strom_problem_create")
+        self.handle = h
+        self.N, self.dx, self.du = src.N, src.dx, src.du
+        self._keep = None  # the library copied the data
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib().strom_problem_destroy(self.handle)
+            self.handle = None
+
+    def relax(self) -> "Sdp":
+        h = C.c_void_p()
+        check(lib().strom_relax(self.handle, C.byref(h)), "strom_relax")
+        return Sdp(h)
+
+
+@dataclass
+class SdpArrays:
+    block_n: np.ndarray
+    block_off: np.ndarray
+    block_kind: np.ndarray
+    block_clique: np.ndarray
+    C: np.ndarray
+    rowptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray
+    b: np.ndarray
+    row_kind: np.ndarray
+    row_clique: np.ndarray
+
+
+class Sdp:
+    def __init__(self, handle):
+        self.handle = handle
+        self.info = N.strom_sdp_info()
+        check(lib().strom_sdp_info_get(handle, C.byref(self.info)), "strom_sdp_info_get")
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib().strom_sdp_destroy(self.handle)
+            self.handle = None
+
+    @property
+    def m(self):
+        return self.info.m
+
+    @property
+    def nsvec(self):
+        return self.info.nsvec
+
+    def export(self) -> SdpArrays:
+        i = self.info
+        a = SdpArrays(np.empty(i.nblocks, np.int32), np.empty(i.nblocks, np.int64), np.empty(i.nblocks, np.int8),
+                      np.empty(i.nblocks, np.int32), np.empty(i.nsvec), np.empty(i.m + 1, np.int64),
+                      np.empty(i.nnz, np.int32), np.empty(i.nnz), np.empty(i.m), np.empty(i.m, np.int8),
+                      np.empty(i.m, np.int32))
+        check(lib().strom_sdp_export(self.handle, _ptr(a.block_n, C.c_int32), _ptr(a.block_off, C.c_int64),
+                                     _ptr(a.block_kind, C.c_int8), _ptr(a.block_clique, C.c_int32),
+                                     _ptr(a.C, C.c_double), _ptr(a.rowptr, C.c_int64), _ptr(a.col, C.c_int32),
+                                     _ptr(a.val, C.c_double), _ptr(a.b, C.c_double), _ptr(a.row_kind, C.c_int8),
+                                     _ptr(a.row_clique, C.c_int32)), "strom_sdp_export")
+        return a
+
+
+def default_options(**kw) -> N.strom_options:
+    o = N.strom_options()
+    lib().strom_options_default(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+@dataclass
+class Result:
+    status: int
+    iterations: int
+    pobj: float
+    dobj: float
+    eta_p: float
+    eta_d: float
+    eta_g: float
+    sigma: float
+    m_kept: int
+
+
+@dataclass
+class Certificate:
+    max_ratio: float
+    lower_bound: float
+    phat: float
+    xi: float
+    hmax: float
+    gmin: float
+    feasible: bool
+    rank_one: bool
+    certified: bool
+    zbar: np.ndarray
+    zhat: np.ndarray
+
+
+class Solver:
+    """strom_solver: sGS-ADMM (Algorithm 1) on a batch of SDPs on the current GPU."""
+
+    def __init__(self, sdps, **opts):
+        self.sdps = list(sdps)
+        arr = (C.c_void_p * len(self.sdps))(*[s.handle.value for s in self.sdps])
+        self.opt = default_options(**opts)
+        h = C.c_void_p()
+        check(lib().strom_solver_create(arr, len(self.sdps), C.byref(self.opt), C.byref(h)), "strom_solver_create")
+        self.handle = h
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib().strom_solver_destroy(self.handle)
+            self.handle = None
+
+    def __len__(self):
+        return lib().strom_solver_count(self.handle)
+
+    def solve(self, stream=None) -> int:
+        return check(lib().strom_solve(self.handle, stream), "strom_solve")
+
+    def step(self, iters, stream=None) -> int:
+        n = C.c_int32()
+        check(lib().strom_solver_step(self.handle, iters, stream, C.byref(n)), "strom_solver_step")
+        return n.value
+
+    def reset(self, i=-1, X0=None, S0=None, sigma=0.0):
+        px = None if X0 is None else _ptr(np.ascontiguousarray(X0, np.float64), C.c_double)
+        ps = None if S0 is None else _ptr(np.ascontiguousarray(S0, np.float64), C.c_double)
+        check(lib().strom_solver_reset(self.handle, i, px, ps, float(sigma)), "strom_solver_reset")
+
+    def result(self, i=0) -> Result:
+        r = N.strom_result()
+        check(lib().strom_get_result(self.handle, i, C.byref(r)), "strom_get_result")
+        return Result(r.status, r.iterations, r.pobj, r.dobj, r.eta_p, r.eta_d, r.eta_g, r.sigma, r.m_kept)
+
+    def state(self, i=0):
+        s = self.sdps[i]
+        X, S, y = np.empty(s.nsvec), np.empty(s.nsvec), np.empty(s.m)
+        check(lib().strom_get_state(self.handle, i, _ptr(X, C.c_double), _ptr(S, C.c_double), _ptr(y, C.c_double)),
+              "strom_get_state")
+        return X, S, y
+
+    def kept_rows(self, i=0):
+        k = np.empty(self.sdps[i].m, np.uint8)
+        check(lib().strom_get_kept_rows(self.handle, i, _ptr(k, C.c_uint8)), "strom_get_kept_rows")
+        return k.astype(bool)
+
+    def moment(self, i, k):
+        s = self.sdps[i]
+        n = int(s.export().block_n[0])
+        M = np.empty((n, n))
+        check(lib().strom_get_moment(self.handle, i, k, _ptr(M, C.c_double)), "strom_get_moment")
+        return M
+
+    def certify(self, i, problem: Problem, rank_tol=1e-4, xi_tol=1e-2) -> Certificate:
+        c = N.strom_certificate()
+        nz = problem.N * (problem.dx + problem.du) + problem.dx
+        zb, zh = np.empty(nz), np.empty(nz)
+        check(lib().strom_certify(self.handle, i, problem.handle, rank_tol, xi_tol, C.byref(c),
+                                  _ptr(zb, C.c_double), _ptr(zh, C.c_double)), "strom_certify")
+        return Certificate(c.max_ratio, c.lower_bound, c.phat, c.xi, c.hmax, c.gmin, bool(c.feasible),
+                           bool(c.rank_one), bool(c.certified), zb, zh)
+
+    # kernel-level entry points (device pointers)
+    @property
+    def nsvec_total(self):
+        return lib().strom_solver_nsvec_total(self.handle)
+
+    @property
+    def m_total(self):
+        return lib().strom_solver_m_total(self.handle)
+
+    def offsets(self, i):
+        so, ro = C.c_int64(), C.c_int64()
+        check(lib().strom_solver_offsets(self.handle, i, C.byref(so), C.byref(ro)), "strom_solver_offsets")
+        return so.value, ro.value
+
+    def kernel_A(self, x_ptr, out_ptr, stream=None):
+        check(lib().strom_kernel_A(self.handle, x_ptr, out_ptr, stream), "strom_kernel_A")
+
+    def kernel_At(self, y_ptr, out_ptr, stream=None):
+        check(lib().strom_kernel_At(self.handle, y_ptr, out_ptr, stream), "strom_kernel_At")
+
+    def kernel_solve(self, r_ptr, y_ptr, stream=None):
+        check(lib().strom_kernel_solve(self.handle, r_ptr, y_ptr, stream), "strom_kernel_solve")
+
+
+class PsdPlan:
+    """strom_psd_plan: PSD projection of a fixed list of svec blocks."""
+
+    def __init__(self, blk_off, blk_n, precision=N.STROM_PREC_FP64):
+        self._off = np.ascontiguousarray(blk_off, np.int64)
+        self._n = np.ascontiguousarray(blk_n, np.int32)
+        h = C.c_void_p()
+        check(lib().strom_psd_plan_create(_ptr(self._off, C.c_int64), _ptr(self._n, C.c_int32), len(self._n),
+                                          precision, C.byref(h)), "strom_psd_plan_create")
+        self.handle = h
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib().strom_psd_plan_destroy(self.handle)
+            self.handle = None
+
+    def execute(self, xb_ptr, out_ptr, lam_ptr=None, stream=None):
+        check(lib().strom_psd_execute(self.handle, xb_ptr, out_ptr, lam_ptr, stream), "strom_psd_execute")
+
+
+def kernel_psd_project(xb_ptr, blk_off, blk_n, precision, out_ptr, stream=None):
+    off = np.ascontiguousarray(blk_off, np.int64)
+    n = np.ascontiguousarray(blk_n, np.int32)
+    check(lib().strom_kernel_psd_project(xb_ptr, _ptr(off, C.c_int64), _ptr(n, C.c_int32), len(n), precision,
+                                         out_ptr, stream), "strom_kernel_psd_project")

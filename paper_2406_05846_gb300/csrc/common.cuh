@@ -1,0 +1,89 @@
+// Device/host helpers shared by the CUDA translation units of libstrom.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <stdexcept>
+#include <string>
+
+#include "internal.h"
+
+#define STROM_CUDA(call)                                                                   \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      throw strom::CudaError(std::string(#call) + ": " + cudaGetErrorString(e_));          \
+  } while (0)
+
+namespace strom {
+
+struct CudaError : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+struct StatusError : std::runtime_error {
+  int status;
+  StatusError(int s, const std::string& m) : std::runtime_error(m), status(s) {}
+};
+
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  void alloc(size_t count) {
+    release();
+    if (count == 0) return;
+    cudaError_t e = cudaMalloc((void**)&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      throw StatusError(STROM_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    n = count;
+  }
+  void upload(const T* h, size_t count, cudaStream_t st = 0) {
+    alloc(count);
+    if (count) STROM_CUDA(cudaMemcpyAsync(p, h, count * sizeof(T), cudaMemcpyHostToDevice, st));
+  }
+  void zero(cudaStream_t st = 0) {
+    if (n) STROM_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), st));
+  }
+};
+
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------
+// PSD projection launcher (psd.cu)
+// ---------------------------------------------------------------------------
+struct PsdClasses {
+  // block ids grouped by size class; classes: n <= 16, <= 40, <= 80, <= 160
+  int count[4] = {0, 0, 0, 0};
+  int start[4] = {0, 0, 0, 0};
+  int max_n[4] = {0, 0, 0, 0};
+};
+
+struct PsdArgs {
+  const double* Xb;            // svec input
+  double* out;                 // svec output
+  const int64_t* blk_off;      // [nblk]
+  const int32_t* blk_n;        // [nblk]
+  const int32_t* blk_list;     // block ids sorted by class
+  const double* blk_inv_sigma; // [nblk] or null: out = (Pi(Xb) - Xb) * inv_sigma
+  const uint8_t* blk_active;   // [nblk] or null: skip inactive blocks
+  double* lam;                 // optional eigenvalues (ascending) at lam_off[b]
+  const int64_t* lam_off;
+  double* topvec;              // optional eigenvector of the largest eigenvalue at lam_off[b]
+  double* vscratch;            // FP64 V storage for the n <= 160 class: [count * 160 * 160]
+};
+
+// precision: STROM_PREC_FP64 or STROM_PREC_FP32
+void psd_launch(const PsdArgs& a, const PsdClasses& c, int precision, cudaStream_t st);
+void psd_configure();  // one-time function attributes (large shared memory)
+
+}  // namespace strom

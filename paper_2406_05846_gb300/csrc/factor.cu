@@ -1,0 +1,334 @@
+// y-solve with the pre-factorised A A^T (Sec. 4, hybrid sparse linear system
+// solver; eq. cholesky), done entirely on the GPU.
+//
+// Structure used (exact algebra, no approximation):
+//  * Each A_mom row ties a duplicate entry p of a monomial to its
+//    representative r: a_p = s_p e_p - s_r e_r. The rows of one monomial form
+//    a "star" whose Gram block is D + s_r^2 1 1^T (D = diag(s_p^2)); it is
+//    inverted by the Sherman-Morrison formula. These rows are always
+//    independent (each owns the entry p).
+//  * Eliminating the stars leaves, on the other rows (A_ineq, A_eq, phi_0,
+//    A_sen), the Schur complement S = A_o diag(omega) A_o^T with
+//    omega_r = 1 / (s_r^2 * #occurrences of the monomial) at representatives
+//    and omega = 1 on localizing entries. Ordered by clique, S is block
+//    tridiagonal and the coupling between cliques k and k+1 runs only through
+//    the consensus rows of clique k (the last rows of its group).
+//  * S is factorised in the order cliques N..1 (natural order inside a
+//    clique) by a Cholesky that skips a row whose pivot is at most
+//    rank_tol * S_ii: that row is linearly dependent on the rows before it
+//    and is removed from the SDP (y = 0 there). Factor blocks: a dense lower
+//    triangular L_k per clique and a coupling E_k = L_k^{-1} S[G_k, cons_{k-1}].
+// All arithmetic is FP64.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "factor.cuh"
+
+namespace strom {
+namespace {
+
+constexpr int FT = 256;  // threads per factor / solve CTA
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// S_ij = sum_p omega_p A_ip A_jp over two sorted CSR rows
+__device__ double sdot(const YsolveDev& d, int64_t ri, int64_t rj) {
+  int64_t a = d.rowptr[ri], ae = d.rowptr[ri + 1];
+  int64_t b = d.rowptr[rj], be = d.rowptr[rj + 1];
+  double s = 0.0;
+  while (a < ae && b < be) {
+    const int ca = d.col[a], cb = d.col[b];
+    if (ca == cb) { s += d.omega[ca] * d.val[a] * d.val[b]; ++a; ++b; }
+    else if (ca < cb) ++a;
+    else ++b;
+  }
+  return s;
+}
+
+// One CTA per (instance, clique): dense lower D_k = S[G_k, G_k], its diagonal,
+// and the coupling right-hand side B_k = S[G_k, cons_{k-1}].
+__global__ void __launch_bounds__(FT) assemble_kernel(YsolveDev d) {
+  const int g = blockIdx.x;  // global group id
+  const int64_t g0 = d.grp_ptr[g];
+  const int m = (int)(d.grp_ptr[g + 1] - g0);
+  double* L = d.fac + d.fac_off[g];
+  double* diag0 = d.diag0 + g0;
+  for (int64_t idx = threadIdx.x; idx < (int64_t)m * m; idx += FT) {
+    const int i = (int)(idx % m), j = (int)(idx / m);  // column-major: i row, j col
+    double v = 0.0;
+    if (i >= j) v = sdot(d, d.oth_rows[g0 + i], d.oth_rows[g0 + j]);
+    L[idx] = v;
+    if (i == j) diag0[i] = v;
+  }
+  const int cprev = d.coup_n[g];
+  if (cprev > 0) {
+    const int64_t pg0 = d.grp_ptr[g - 1];
+    const int pm = (int)(d.grp_ptr[g] - pg0);
+    double* B = d.coup + d.coup_off[g];
+    for (int64_t idx = threadIdx.x; idx < (int64_t)m * cprev; idx += FT) {
+      const int i = (int)(idx % m), c = (int)(idx / m);
+      B[idx] = sdot(d, d.oth_rows[g0 + i], d.oth_rows[pg0 + pm - cprev + c]);
+    }
+  }
+}
+
+// One CTA per instance: the chain factorisation, cliques N..1.
+__global__ void __launch_bounds__(FT) chain_factor_kernel(YsolveDev d, double rank_tol) {
+  const int inst = blockIdx.x;
+  const int gbeg = d.inst_grp[inst], gend = d.inst_grp[inst + 1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __shared__ double s_piv;
+  __shared__ int s_keep;
+  for (int g = gend - 1; g >= gbeg; --g) {
+    const int64_t g0 = d.grp_ptr[g];
+    const int m = (int)(d.grp_ptr[g + 1] - g0);
+    double* L = d.fac + d.fac_off[g];
+    // Schur update from the clique factored just before: D[cons, cons] -= E^T E
+    if (g + 1 < gend) {
+      const int cn = d.coup_n[g + 1];
+      const int64_t ng0 = d.grp_ptr[g + 1];
+      const int nm = (int)(d.grp_ptr[g + 2] - ng0);
+      const double* E = d.coup + d.coup_off[g + 1];
+      for (int pair = warp; pair < cn * cn; pair += FT / 32) {
+        const int a = pair % cn, b = pair / cn;
+        if (a < b) continue;
+        double s = 0.0;
+        for (int r = lane; r < nm; r += 32) s += E[(int64_t)a * nm + r] * E[(int64_t)b * nm + r];
+        s = warp_sum(s);
+        if (lane == 0) {
+          const int i = m - cn + a, j = m - cn + b;
+          L[(int64_t)j * m + i] -= s;
+        }
+      }
+      __syncthreads();
+    }
+    // pivot-skipping right-looking Cholesky
+    for (int j = 0; j < m; ++j) {
+      if (threadIdx.x == 0) {
+        const double piv = L[(int64_t)j * m + j];
+        const double ref = d.diag0[g0 + j];
+        const int keep = (ref > 0.0) && (piv > rank_tol * ref);
+        s_keep = keep;
+        s_piv = keep ? sqrt(piv) : 1.0;
+        d.keep[d.oth_rows[g0 + j]] = (uint8_t)keep;
+        L[(int64_t)j * m + j] = s_piv;
+      }
+      __syncthreads();
+      const int keep = s_keep;
+      const double inv = 1.0 / s_piv;
+      double* colj = L + (int64_t)j * m;
+      for (int i = j + 1 + threadIdx.x; i < m; i += FT) colj[i] = keep ? colj[i] * inv : 0.0;
+      __syncthreads();
+      if (keep) {
+        for (int l = j + 1 + warp; l < m; l += FT / 32) {
+          const double ljl = colj[l];
+          if (ljl == 0.0) continue;
+          double* coll = L + (int64_t)l * m;
+          for (int i = l + lane; i < m; i += 32) coll[i] -= colj[i] * ljl;
+        }
+      }
+      __syncthreads();
+    }
+    // coupling E_g = L_g^{-1} B_g (one warp per right-hand side)
+    const int cprev = d.coup_n[g];
+    if (cprev > 0) {
+      double* B = d.coup + d.coup_off[g];
+      for (int c = warp; c < cprev; c += FT / 32) {
+        double* e = B + (int64_t)c * m;
+        for (int j = 0; j < m; ++j) {
+          const double* colj = L + (int64_t)j * m;
+          double ej = 0.0;
+          if (lane == 0) ej = d.keep[d.oth_rows[g0 + j]] ? e[j] / colj[j] : 0.0;
+          ej = __shfl_sync(0xffffffffu, ej, 0);
+          if (lane == 0) e[j] = ej;
+          if (ej != 0.0)
+            for (int i = j + 1 + lane; i < m; i += 32) e[i] -= colj[i] * ej;
+          __syncwarp();
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// solve kernels
+// ---------------------------------------------------------------------------
+
+// rho at every representative with duplicates:
+// rho_r = c * sum_p r_p / s_p^2 / (1 + c d) / s_r   (c = s_r^2, d = sum 1/s_p^2)
+__global__ void star_pre_kernel(YsolveDev d, const double* __restrict__ r, double* __restrict__ rho) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.nclass) return;
+  if (d.inst_active && !d.inst_active[d.star_inst[c]]) return;
+  double acc = 0.0;
+  for (int32_t q = d.star_ptr[c]; q < d.star_ptr[c + 1]; ++q) acc += r[d.star_row[q]] * d.star_inv_s2[q];
+  const double cc = d.star_c[c];
+  const int64_t rep = d.star_rep[c];
+  rho[rep] = cc * acc / (1.0 + cc * d.star_d[c]) * d.inv_rep_s[rep];
+}
+
+// t_i = r_i + sum_p A_ip rho_p for every other row (written into y)
+__global__ void other_rhs_kernel(YsolveDev d, const double* __restrict__ r, const double* __restrict__ rho,
+                                 double* __restrict__ y) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= d.noth) return;
+  const int64_t row = d.oth_rows[q];
+  if (d.inst_active && !d.inst_active[d.row_inst[row]]) return;
+  double t = r[row];
+  for (int64_t e = d.rowptr[row]; e < d.rowptr[row + 1]; ++e) t += d.val[e] * rho[d.col[e]];
+  y[row] = d.keep[row] ? t : 0.0;
+}
+
+// block forward / backward substitution along the chain; one CTA per instance
+__global__ void __launch_bounds__(FT) chain_solve_kernel(YsolveDev d, double* __restrict__ y) {
+  const int inst = blockIdx.x;
+  if (d.inst_active && !d.inst_active[inst]) return;
+  const int gbeg = d.inst_grp[inst], gend = d.inst_grp[inst + 1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  extern __shared__ double sh[];  // [max group size]
+  // forward: groups gend-1 .. gbeg,  w_g = L_g^{-1} (t_g - F_g w_{g+1})
+  for (int g = gend - 1; g >= gbeg; --g) {
+    const int64_t g0 = d.grp_ptr[g];
+    const int m = (int)(d.grp_ptr[g + 1] - g0);
+    const double* L = d.fac + d.fac_off[g];
+    for (int i = threadIdx.x; i < m; i += FT) sh[i] = y[d.oth_rows[g0 + i]];
+    __syncthreads();
+    if (g + 1 < gend) {
+      const int cn = d.coup_n[g + 1];
+      const int64_t ng0 = d.grp_ptr[g + 1];
+      const int nm = (int)(d.grp_ptr[g + 2] - ng0);
+      const double* E = d.coup + d.coup_off[g + 1];
+      for (int a = warp; a < cn; a += FT / 32) {
+        double s = 0.0;
+        for (int rr = lane; rr < nm; rr += 32) s += E[(int64_t)a * nm + rr] * y[d.oth_rows[ng0 + rr]];
+        s = warp_sum(s);
+        if (lane == 0) sh[m - cn + a] -= s;
+      }
+      __syncthreads();
+    }
+    for (int jb = 0; jb < m; jb += 32) {
+      const int je = min(jb + 32, m);
+      if (warp == 0) {
+        const int j = jb + lane;
+        double tj = (j < je) ? sh[j] : 0.0;
+        const uint8_t kj = (j < je) ? d.keep[d.oth_rows[g0 + j]] : 0;
+        for (int jj = jb; jj < je; ++jj) {
+          double w = 0.0;
+          if (lane == jj - jb) w = kj ? tj / L[(int64_t)jj * m + jj] : 0.0;
+          w = __shfl_sync(0xffffffffu, w, jj - jb);
+          if (j > jj && j < je) tj -= L[(int64_t)jj * m + j] * w;
+          if (lane == jj - jb) tj = w;
+        }
+        if (j < je) sh[j] = tj;
+      }
+      __syncthreads();
+      for (int i = je + threadIdx.x; i < m; i += FT) {
+        double s = 0.0;
+        for (int jj = jb; jj < je; ++jj) s += L[(int64_t)jj * m + i] * sh[jj];
+        sh[i] -= s;
+      }
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < m; i += FT) y[d.oth_rows[g0 + i]] = sh[i];
+    __syncthreads();
+  }
+  // backward: groups gbeg .. gend-1,  y_g = L_g^{-T} (w_g - E_g y_{g-1}[cons])
+  for (int g = gbeg; g < gend; ++g) {
+    const int64_t g0 = d.grp_ptr[g];
+    const int m = (int)(d.grp_ptr[g + 1] - g0);
+    const double* L = d.fac + d.fac_off[g];
+    const int cprev = d.coup_n[g];
+    const double* E = d.coup + d.coup_off[g];
+    const int64_t pg0 = (g > gbeg) ? d.grp_ptr[g - 1] : 0;
+    const int pm = (g > gbeg) ? (int)(d.grp_ptr[g] - pg0) : 0;
+    for (int i = threadIdx.x; i < m; i += FT) {
+      double w = y[d.oth_rows[g0 + i]];
+      for (int c = 0; c < cprev; ++c) w -= E[(int64_t)c * m + i] * y[d.oth_rows[pg0 + pm - cprev + c]];
+      sh[i] = w;
+    }
+    __syncthreads();
+    const int nb = (m + 31) / 32;
+    for (int b = nb - 1; b >= 0; --b) {
+      const int jb = b * 32, je = min(jb + 32, m);
+      // w_j -= sum_{i >= je} L[i][j] y_i for j in [jb, je)
+      for (int j = jb + warp; j < je; j += FT / 32) {
+        const double* colj = L + (int64_t)j * m;
+        double s = 0.0;
+        for (int i = je + lane; i < m; i += 32) s += colj[i] * sh[i];
+        s = warp_sum(s);
+        if (lane == 0) sh[j] -= s;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        const int j = jb + lane;
+        double wj = (j < je) ? sh[j] : 0.0;
+        const uint8_t kj = (j < je) ? d.keep[d.oth_rows[g0 + j]] : 0;
+        for (int jj = je - 1; jj >= jb; --jj) {
+          double v = 0.0;
+          if (lane == jj - jb) v = kj ? wj / L[(int64_t)jj * m + jj] : 0.0;
+          v = __shfl_sync(0xffffffffu, v, jj - jb);
+          if (j < jj) wj -= L[(int64_t)j * m + jj] * v;
+          if (lane == jj - jb) wj = v;
+        }
+        if (j < je) sh[j] = wj;
+      }
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < m; i += FT) y[d.oth_rows[g0 + i]] = sh[i];
+    __syncthreads();
+  }
+}
+
+// star rows: y_alpha = (D + c 1 1^T)^{-1} (r_alpha + c gamma 1),
+// gamma = sum_{other rows i} A_{i,rep} y_i / s_rep
+__global__ void star_post_kernel(YsolveDev d, const double* __restrict__ r, double* __restrict__ y) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d.nclass) return;
+  if (d.inst_active && !d.inst_active[d.star_inst[c]]) return;
+  const int64_t rep = d.star_rep[c];
+  double gam = 0.0;
+  for (int64_t e = d.atptr[rep]; e < d.atptr[rep + 1]; ++e) {
+    const int32_t row = d.atrow[e];
+    if (d.row_kind[row] != STROM_ROW_MOM) gam += d.atval[e] * y[row];
+  }
+  gam *= d.inv_rep_s[rep];
+  const double cc = d.star_c[c];
+  double su = 0.0;
+  for (int32_t q = d.star_ptr[c]; q < d.star_ptr[c + 1]; ++q) su += (r[d.star_row[q]] + cc * gam) * d.star_inv_s2[q];
+  const double corr = cc * su / (1.0 + cc * d.star_d[c]);
+  for (int32_t q = d.star_ptr[c]; q < d.star_ptr[c + 1]; ++q) {
+    const double is2 = d.star_inv_s2[q];
+    y[d.star_row[q]] = (r[d.star_row[q]] + cc * gam) * is2 - is2 * corr;
+  }
+}
+
+}  // namespace
+
+void ysolve_factor(const YsolveDev& d, int ngroups, int ninst, double rank_tol, cudaStream_t st) {
+  assemble_kernel<<<ngroups, FT, 0, st>>>(d);
+  STROM_CUDA(cudaGetLastError());
+  chain_factor_kernel<<<ninst, FT, 0, st>>>(d, rank_tol);
+  STROM_CUDA(cudaGetLastError());
+}
+
+void ysolve_apply(const YsolveDev& d, int ninst, int max_group, const double* r, double* y, double* rho,
+                  cudaStream_t st) {
+  if (d.nclass > 0) {
+    star_pre_kernel<<<ceil_div(d.nclass, 256), 256, 0, st>>>(d, r, rho);
+    STROM_CUDA(cudaGetLastError());
+  }
+  other_rhs_kernel<<<ceil_div(d.noth, 256), 256, 0, st>>>(d, r, rho, y);
+  STROM_CUDA(cudaGetLastError());
+  chain_solve_kernel<<<ninst, FT, sizeof(double) * max_group, st>>>(d, y);
+  STROM_CUDA(cudaGetLastError());
+  if (d.nclass > 0) {
+    star_post_kernel<<<ceil_div(d.nclass, 256), 256, 0, st>>>(d, r, y);
+    STROM_CUDA(cudaGetLastError());
+  }
+}
+
+}  // namespace strom

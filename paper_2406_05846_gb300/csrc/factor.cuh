@@ -1,0 +1,50 @@
+// Device-side view of the y-solve data (factor.cu).
+#pragma once
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace strom {
+
+struct YsolveDev {
+  // A (CSR over the whole batch) and A^T (CSR over svec positions)
+  const int64_t* rowptr;
+  const int32_t* col;
+  const double* val;
+  const int64_t* atptr;
+  const int32_t* atrow;
+  const double* atval;
+  const int8_t* row_kind;
+  const int32_t* row_inst;
+  // star elimination
+  int64_t nclass;
+  const int64_t* star_rep;
+  const double* star_c;
+  const double* star_d;
+  const int32_t* star_ptr;
+  const int64_t* star_row;
+  const double* star_inv_s2;
+  const int32_t* star_inst;
+  const double* omega;
+  const double* inv_rep_s;
+  // groups of other rows: grp_ptr over all (instance, clique) groups
+  int64_t noth;
+  const int64_t* oth_rows;
+  const int64_t* grp_ptr;
+  const int32_t* inst_grp;   // [ninst+1] first group of each instance
+  const int32_t* coup_n;     // [ngroups] consensus rows of the previous group coupled to this one
+  // factor storage
+  double* fac;
+  const int64_t* fac_off;
+  double* coup;
+  const int64_t* coup_off;
+  double* diag0;             // [noth]
+  uint8_t* keep;             // [m_total]
+  const uint8_t* inst_active;  // nullable
+};
+
+void ysolve_factor(const YsolveDev& d, int ngroups, int ninst, double rank_tol, cudaStream_t st);
+void ysolve_apply(const YsolveDev& d, int ninst, int max_group, const double* r, double* y, double* rho,
+                  cudaStream_t st);
+
+}  // namespace strom

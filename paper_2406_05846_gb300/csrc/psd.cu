@@ -1,0 +1,380 @@
+// PSD cone projection of many small symmetric blocks (Sec. 4, parallel PSD
+// cone projection): Pi(X_beta) = Q max(0, W) Q^T from X_beta = Q W Q^T.
+//
+// One CTA per block. The block is unpacked from svec into shared memory and
+// diagonalised by the cyclic two-sided Jacobi method with the round-robin
+// (tournament) ordering: in each round the np/2 rotations act on disjoint
+// index pairs, so all of them are applied at once. Every 2x2 sub-block
+// A[{p1,q1},{p2,q2}] is owned by one thread, which applies J1^T (.) J2 in
+// registers, so a round needs one barrier after the rotation parameters and
+// one after the update. The 2x2 symmetric Schur rotation is the one of
+// Golub & Van Loan (Matrix Computations, Sec. 8.5). Sweeps stop when the sum
+// of squares of the off-diagonal entries met during a sweep is below
+// tol^2 ||A||_F^2. The recombination W = V diag(sqrt(max(lam, 0))),
+// Pi = W W^T writes svec output directly, optionally fused with the ADMM
+// update S = (Pi(X_b) - X_b) / sigma (eq. solve-S).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+namespace strom {
+namespace {
+
+template <typename T> __device__ __forceinline__ T dsqrt_(T x);
+template <> __device__ __forceinline__ double dsqrt_<double>(double x) { return sqrt(x); }
+template <> __device__ __forceinline__ float dsqrt_<float>(float x) { return __fsqrt_rn(x); }
+// 1 / sqrt(x) with correctly rounded sqrt and division: an approximate
+// reciprocal square root would make every rotation slightly non-orthogonal
+// and the error would grow with the number of rotations applied to V.
+template <typename T> __device__ __forceinline__ T drsqrt_(T x);
+template <> __device__ __forceinline__ double drsqrt_<double>(double x) { return 1.0 / sqrt(x); }
+template <> __device__ __forceinline__ float drsqrt_<float>(float x) { return __fdiv_rn(1.0f, __fsqrt_rn(x)); }
+
+template <int NT>
+__device__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < NT / 32; ++i) s += red[i];
+  return s;
+}
+
+template <typename T, int NP, int NT, bool VSMEM>
+struct JacobiSmem {
+  static constexpr int LD = NP + 1;
+  static constexpr size_t a_bytes = sizeof(T) * NP * LD;
+  static constexpr size_t v_bytes = VSMEM ? sizeof(T) * NP * LD : 0;
+  static constexpr size_t rot_bytes = (sizeof(T) * 3 + sizeof(int) * 2) * (NP / 2);
+  static constexpr size_t red_bytes = sizeof(double) * (NT / 32 + 2);
+  static constexpr size_t total = a_bytes + v_bytes + rot_bytes + red_bytes + 64;
+};
+
+template <typename T, int NP, int NT, bool VSMEM>
+__global__ void __launch_bounds__(NT) jacobi_psd_kernel(PsdArgs a, int list_start, double tol, int max_sweeps) {
+  using SM = JacobiSmem<T, NP, NT, VSMEM>;
+  constexpr int LD = SM::LD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* A = reinterpret_cast<T*>(smem_raw);
+  T* V = VSMEM ? reinterpret_cast<T*>(smem_raw + SM::a_bytes)
+               : reinterpret_cast<T*>(a.vscratch) + (size_t)blockIdx.x * NP * LD;
+  T* sT = reinterpret_cast<T*>(smem_raw + SM::a_bytes + SM::v_bytes);
+  T* sS = sT + NP / 2;
+  T* sU = sS + NP / 2;
+  int* sP = reinterpret_cast<int*>(sU + NP / 2);
+  int* sQ = sP + NP / 2;
+  double* red = reinterpret_cast<double*>(smem_raw + SM::a_bytes + SM::v_bytes + SM::rot_bytes + 16);
+  // keep the reduction buffer 8-byte aligned
+  red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(red) + 7) & ~uintptr_t(7));
+
+  const int tid = threadIdx.x;
+  const int bid = a.blk_list[list_start + blockIdx.x];
+  if (a.blk_active != nullptr && a.blk_active[bid] == 0) return;
+  const int n = a.blk_n[bid];
+  const int np = n + (n & 1);
+  const int64_t off = a.blk_off[bid];
+  const double* __restrict__ xb = a.Xb + off;
+
+  // ---- unpack svec -> full symmetric matrix, V = I
+  double fro = 0.0;
+  for (int idx = tid; idx < np * np; idx += NT) {
+    const int i = idx % np, j = idx / np;
+    T v = T(0);
+    if (i < n && j < n) {
+      const int ii = min(i, j), jj = max(i, j);
+      const double x = xb[(int64_t)jj * (jj + 1) / 2 + ii];
+      const double e = (ii == jj) ? x : x * 0.70710678118654752440;
+      v = (T)e;
+      fro += e * e;
+    }
+    A[i * LD + j] = v;
+    V[i * LD + j] = (i == j) ? T(1) : T(0);
+  }
+  fro = block_sum<NT>(fro, red);   // contains a barrier
+
+  // ---- cyclic Jacobi sweeps, round-robin ordering
+  const int half = np / 2;
+  const int nA = half * half;
+  const int nV = np * half;
+  const double thr = tol * tol * fro;
+  for (int sweep = 0; sweep < max_sweeps && np > 1; ++sweep) {
+    double off_sum = 0.0;
+    for (int r = 0; r < np - 1; ++r) {
+      if (tid < half) {
+        const int t = tid;
+        const int pa = (t == 0) ? 0 : ((t - 1 + r) % (np - 1)) + 1;
+        const int pb = ((np - 2 - t + r) % (np - 1)) + 1;
+        const int p = min(pa, pb), q = max(pa, pb);
+        const T app = A[p * LD + p], aqq = A[q * LD + q], apq = A[p * LD + q];
+        // tangent t, sine s and tau = s / (1 + c) of the 2x2 symmetric Schur rotation
+        T tt = T(0), s = T(0), ta = T(0);
+        off_sum += (double)apq * (double)apq;
+        if (apq != T(0)) {
+          const T tau = (aqq - app) / (T(2) * apq);
+          const T at = fabs(tau);
+          if (at > T(1e15)) tt = T(0.5) / tau;  // 1 + tau^2 would lose tau's size
+          else tt = (tau >= T(0) ? T(1) : T(-1)) / (at + dsqrt_<T>(T(1) + tau * tau));
+          const T c = drsqrt_<T>(T(1) + tt * tt);
+          s = tt * c;
+          ta = s / (T(1) + c);
+        }
+        sP[t] = p; sQ[t] = q; sT[t] = tt; sS[t] = s; sU[t] = ta;
+      }
+      __syncthreads();
+      for (int item = tid; item < nA + nV; item += NT) {
+        if (item < nA) {
+          const int t1 = item / half, t2 = item - (item / half) * half;
+          const int p1 = sP[t1], q1 = sQ[t1], p2 = sP[t2], q2 = sQ[t2];
+          const T x00 = A[p1 * LD + p2], x01 = A[p1 * LD + q2];
+          const T x10 = A[q1 * LD + p2], x11 = A[q1 * LD + q2];
+          T y00, y01, y10, y11;
+          if (t1 == t2) {
+            // annihilated pair: a_pp - t a_pq, a_qq + t a_pq, a_pq = 0
+            const T tt = sT[t1];
+            y00 = x00 - tt * x01;
+            y11 = x11 + tt * x01;
+            y01 = T(0);
+            y10 = T(0);
+          } else {
+            // J1^T X J2 written as corrections x - s (y + tau x) (Rutishauser):
+            // no rounding bias from c ~ 1 when the rotation is small
+            const T s1 = sS[t1], u1 = sU[t1], s2 = sS[t2], u2 = sU[t2];
+            const T r00 = x00 - s1 * (x10 + u1 * x00), r10 = x10 + s1 * (x00 - u1 * x10);
+            const T r01 = x01 - s1 * (x11 + u1 * x01), r11 = x11 + s1 * (x01 - u1 * x11);
+            y00 = r00 - s2 * (r01 + u2 * r00);
+            y01 = r01 + s2 * (r00 - u2 * r01);
+            y10 = r10 - s2 * (r11 + u2 * r10);
+            y11 = r11 + s2 * (r10 - u2 * r11);
+          }
+          A[p1 * LD + p2] = y00; A[p1 * LD + q2] = y01;
+          A[q1 * LD + p2] = y10; A[q1 * LD + q2] = y11;
+        } else {
+          const int it = item - nA;
+          const int k = it / half, t = it - (it / half) * half;
+          const int p = sP[t], q = sQ[t];
+          const T s = sS[t], u = sU[t];
+          const T vp = V[k * LD + p], vq = V[k * LD + q];
+          V[k * LD + p] = vp - s * (vq + u * vp);
+          V[k * LD + q] = vq + s * (vp - u * vq);
+        }
+      }
+      __syncthreads();
+    }
+    off_sum = block_sum<NT>(off_sum, red);
+    if (off_sum <= thr) break;
+  }
+
+  // ---- eigen outputs (ascending eigenvalues, top eigenvector)
+  if (a.lam != nullptr || a.topvec != nullptr) {
+    const int64_t lo = a.lam_off[bid];
+    if (a.lam != nullptr) {
+      for (int i = tid; i < n; i += NT) {
+        const T li = A[i * LD + i];
+        int rank = 0;
+        for (int j = 0; j < n; ++j) {
+          const T lj = A[j * LD + j];
+          rank += (lj < li) || (lj == li && j < i);
+        }
+        a.lam[lo + rank] = (double)li;
+      }
+    }
+    if (a.topvec != nullptr) {
+      __shared__ int s_arg;
+      if (tid == 0) {
+        int best = 0;
+        for (int j = 1; j < n; ++j) if (A[j * LD + j] > A[best * LD + best]) best = j;
+        s_arg = best;
+      }
+      __syncthreads();
+      const int kk = s_arg;
+      for (int i = tid; i < n; i += NT) a.topvec[lo + i] = (double)V[i * LD + kk];
+    }
+    __syncthreads();
+  }
+  if (a.out == nullptr) return;
+
+  // ---- recombination Pi = W W^T with W = V diag(sqrt(max(lam, 0)))
+  for (int idx = tid; idx < n * np; idx += NT) {
+    const int i = idx / np, k = idx - (idx / np) * np;
+    const T lk = (k < n) ? A[k * LD + k] : T(0);
+    V[i * LD + k] = (lk > T(0)) ? V[i * LD + k] * dsqrt_<T>(lk) : T(0);
+  }
+  __syncthreads();
+  const int nt = n * (n + 1) / 2;
+  const double inv_sigma = (a.blk_inv_sigma != nullptr) ? a.blk_inv_sigma[bid] : 0.0;
+  double* __restrict__ out = a.out + off;
+  for (int idx = tid; idx < nt; idx += NT) {
+    int j = (int)((sqrt(8.0 * idx + 1.0) - 1.0) * 0.5);
+    while ((j + 1) * (j + 2) / 2 <= idx) ++j;
+    while (j * (j + 1) / 2 > idx) --j;
+    const int i = idx - j * (j + 1) / 2;
+    const T* wi = V + i * LD;
+    const T* wj = V + j * LD;
+    T acc = T(0);
+    for (int k = 0; k < n; ++k) acc += wi[k] * wj[k];
+    double x = (double)acc;
+    if (i != j) x *= 1.41421356237309504880;
+    if (a.blk_inv_sigma != nullptr) x = (x - xb[idx]) * inv_sigma;
+    out[idx] = x;
+  }
+}
+
+template <typename T, int NP, int NT, bool VSMEM>
+void set_attr() {
+  using SM = JacobiSmem<T, NP, NT, VSMEM>;
+  STROM_CUDA(cudaFuncSetAttribute(jacobi_psd_kernel<T, NP, NT, VSMEM>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM::total));
+}
+
+template <typename T, int NP, int NT, bool VSMEM>
+void launch_class(const PsdArgs& a, int start, int count, double tol, int sweeps, cudaStream_t st) {
+  if (count == 0) return;
+  using SM = JacobiSmem<T, NP, NT, VSMEM>;
+  jacobi_psd_kernel<T, NP, NT, VSMEM><<<count, NT, SM::total, st>>>(a, start, tol, sweeps);
+  STROM_CUDA(cudaGetLastError());
+}
+
+}  // namespace
+
+void psd_configure() {
+  static bool done = false;
+  if (done) return;
+  set_attr<double, 16, 64, true>();
+  set_attr<double, 40, 128, true>();
+  set_attr<double, 80, 256, true>();
+  set_attr<double, 160, 512, false>();
+  set_attr<float, 16, 64, true>();
+  set_attr<float, 40, 128, true>();
+  set_attr<float, 80, 256, true>();
+  set_attr<float, 160, 512, true>();
+  done = true;
+}
+
+void psd_launch(const PsdArgs& a, const PsdClasses& c, int precision, cudaStream_t st) {
+  psd_configure();
+  if (precision == STROM_PREC_FP64) {
+    const double tol = 1e-14;
+    const int sw = 30;
+    launch_class<double, 16, 64, true>(a, c.start[0], c.count[0], tol, sw, st);
+    launch_class<double, 40, 128, true>(a, c.start[1], c.count[1], tol, sw, st);
+    launch_class<double, 80, 256, true>(a, c.start[2], c.count[2], tol, sw, st);
+    launch_class<double, 160, 512, false>(a, c.start[3], c.count[3], tol, sw, st);
+  } else {
+    const double tol = 2e-6;
+    const int sw = 20;
+    launch_class<float, 16, 64, true>(a, c.start[0], c.count[0], tol, sw, st);
+    launch_class<float, 40, 128, true>(a, c.start[1], c.count[1], tol, sw, st);
+    launch_class<float, 80, 256, true>(a, c.start[2], c.count[2], tol, sw, st);
+    launch_class<float, 160, 512, true>(a, c.start[3], c.count[3], tol, sw, st);
+  }
+}
+
+}  // namespace strom
+
+// ---------------------------------------------------------------------------
+// C ABI: PSD projection plans
+// ---------------------------------------------------------------------------
+struct strom_psd_plan {
+  int nblk = 0;
+  int precision = STROM_PREC_FP64;
+  strom::PsdClasses cls;
+  strom::DevBuf<int64_t> off, lam_off;
+  strom::DevBuf<int32_t> n, list;
+  strom::DevBuf<double> vscratch;
+};
+
+namespace strom {
+int class_of(int n) { return n <= 16 ? 0 : n <= 40 ? 1 : n <= 80 ? 2 : 3; }
+
+void build_classes(const int32_t* blk_n, int nblk, std::vector<int32_t>& list, PsdClasses& c) {
+  std::vector<std::vector<int32_t>> per(4);
+  for (int i = 0; i < nblk; ++i) per[class_of(blk_n[i])].push_back(i);
+  list.clear();
+  for (int k = 0; k < 4; ++k) {
+    c.start[k] = (int)list.size();
+    c.count[k] = (int)per[k].size();
+    for (int b : per[k]) { list.push_back(b); c.max_n[k] = std::max(c.max_n[k], blk_n[b]); }
+  }
+}
+}  // namespace strom
+
+extern "C" int strom_psd_plan_create(const int64_t* blk_off, const int32_t* blk_n, int32_t nblk, int32_t precision,
+                                     strom_psd_plan** out) {
+  try {
+    if (!out || nblk < 0 || (nblk > 0 && (!blk_off || !blk_n)))
+      throw strom::StatusError(STROM_ERR_INVALID, "strom_psd_plan_create: bad arguments");
+    if (precision != STROM_PREC_FP64 && precision != STROM_PREC_FP32)
+      throw strom::StatusError(STROM_ERR_INVALID, "strom_psd_plan_create: precision must be FP64 or FP32");
+    for (int i = 0; i < nblk; ++i)
+      if (blk_n[i] < 1 || blk_n[i] > 160 || blk_off[i] < 0)
+        throw strom::StatusError(STROM_ERR_INVALID, "strom_psd_plan_create: block size must be in 1..160");
+    auto* p = new strom_psd_plan();
+    p->nblk = nblk;
+    p->precision = precision;
+    std::vector<int32_t> list;
+    strom::build_classes(blk_n, nblk, list, p->cls);
+    std::vector<int64_t> lo(nblk);
+    int64_t acc = 0;
+    for (int i = 0; i < nblk; ++i) { lo[i] = acc; acc += blk_n[i]; }
+    p->off.upload(blk_off, nblk);
+    p->n.upload(blk_n, nblk);
+    p->list.upload(list.data(), list.size());
+    p->lam_off.upload(lo.data(), nblk);
+    if (precision == STROM_PREC_FP64 && p->cls.count[3] > 0) p->vscratch.alloc((size_t)p->cls.count[3] * 160 * 161);
+    STROM_CUDA(cudaDeviceSynchronize());
+    *out = p;
+    return STROM_OK;
+  } catch (const strom::StatusError& e) {
+    strom::set_error(e.what());
+    return e.status;
+  } catch (const std::exception& e) {
+    strom::set_error(e.what());
+    return STROM_ERR_CUDA;
+  }
+}
+
+extern "C" void strom_psd_plan_destroy(strom_psd_plan* p) { delete p; }
+
+extern "C" int strom_psd_execute(strom_psd_plan* p, const double* Xb_dev, double* P_dev, double* lam_dev, void* stream) {
+  try {
+    if (!p || !Xb_dev || (!P_dev && !lam_dev) || (P_dev != nullptr && P_dev == Xb_dev))
+      throw strom::StatusError(STROM_ERR_INVALID, "strom_psd_execute: bad arguments");
+    strom::PsdArgs a{};
+    a.Xb = Xb_dev;
+    a.out = P_dev;
+    a.blk_off = p->off.p;
+    a.blk_n = p->n.p;
+    a.blk_list = p->list.p;
+    a.lam = lam_dev;
+    a.lam_off = p->lam_off.p;
+    a.vscratch = p->vscratch.p;
+    strom::psd_launch(a, p->cls, p->precision, (cudaStream_t)stream);
+    return STROM_OK;
+  } catch (const strom::StatusError& e) {
+    strom::set_error(e.what());
+    return e.status;
+  } catch (const std::exception& e) {
+    strom::set_error(e.what());
+    return STROM_ERR_CUDA;
+  }
+}
+
+extern "C" int strom_kernel_psd_project(const double* Xb_dev, const int64_t* blk_off, const int32_t* blk_n,
+                                        int32_t nblk, int32_t precision, double* P_dev, void* stream) {
+  strom_psd_plan* p = nullptr;
+  int st = strom_psd_plan_create(blk_off, blk_n, nblk, precision, &p);
+  if (st != STROM_OK) return st;
+  st = strom_psd_execute(p, Xb_dev, P_dev, nullptr, stream);
+  if (st == STROM_OK) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) { strom::set_error(cudaGetErrorString(e)); st = STROM_ERR_CUDA; }
+  }
+  strom_psd_plan_destroy(p);
+  return st;
+}

@@ -1,0 +1,698 @@
+// Batched sGS-ADMM solver (Algorithm 1) behind the C ABI: setup (upload, row
+// reduction + factorisation of A A^T), the iteration loop captured as a CUDA
+// graph, results, state access and the kernel-level entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <vector>
+
+#include "admm.cuh"
+#include "common.cuh"
+#include "factor.cuh"
+
+namespace strom {
+void build_classes(const int32_t* blk_n, int nblk, std::vector<int32_t>& list, PsdClasses& c);
+}
+
+using namespace strom;
+
+namespace {
+constexpr int64_t kChunk = 4096;
+
+struct InstMeta {
+  int N, nv, dx, du;
+  int64_t nsvec, m;
+  std::vector<int32_t> block_n, block_clique;
+  std::vector<int64_t> block_off;  // local
+  std::vector<int8_t> block_kind;
+  std::vector<double> b;
+};
+}  // namespace
+
+struct strom_solver {
+  strom_options opt{};
+  int ninst = 0;
+  std::vector<InstMeta> meta;
+  std::vector<int64_t> svec_off, row_off;  // [ninst+1]
+  int64_t nsvec = 0, m = 0;
+  int nblk = 0, ngroups = 0, max_group = 0;
+  std::vector<int64_t> inst_blk_off;  // [ninst+1] first global block of instance
+  std::vector<int64_t> m_kept;
+  // device data
+  DevBuf<int64_t> rowptr, atptr, star_rep, star_row, oth_rows, grp_ptr, fac_off, coup_off, blk_off, lam_off;
+  DevBuf<int32_t> col, atrow, row_inst, star_ptr, star_inst, inst_grp, coup_n, blk_n, blk_list, blk_inst;
+  DevBuf<int32_t> inst_svec_chunk, inst_row_chunk, iters, n_active;
+  DevBuf<double> val, atval, b, C, omega, inv_rep_s, star_c, star_d, star_inv_s2, fac, coup, diag0;
+  DevBuf<double> X, S, Xb, y, yh, r, rho, norm_b, norm_C, sigma, stats, part_svec, part_rows, blk_inv_sigma;
+  DevBuf<double> vscratch, tmp_svec, lam, topvec;
+  DevBuf<int8_t> row_kind;
+  DevBuf<uint8_t> keep, inst_active, inst_flag, inst_prec, blk_act32, blk_act64;
+  DevBuf<Chunk> svec_chunks, row_chunks;
+  PsdClasses cls;
+  YsolveDev yd{};
+  AdmmDev ad{};
+  AdmmParams prm{};
+  cudaStream_t stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  cudaGraph_t graph_def = nullptr;
+  ~strom_solver() {
+    if (graph) cudaGraphExecDestroy(graph);
+    if (graph_def) cudaGraphDestroy(graph_def);
+    if (stream) cudaStreamDestroy(stream);
+  }
+};
+
+namespace {
+
+template <typename F>
+int guard(F&& f) {
+  try {
+    return f();
+  } catch (const StatusError& e) {
+    set_error(e.what());
+    return e.status;
+  } catch (const CudaError& e) {
+    set_error(e.what());
+    return STROM_ERR_CUDA;
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return STROM_ERR_OOM;
+  } catch (const std::exception& e) {
+    set_error(e.what());
+    return STROM_ERR_INVALID;
+  }
+}
+
+void make_chunks(const std::vector<int64_t>& off, std::vector<Chunk>& ch, std::vector<int32_t>& first) {
+  ch.clear();
+  first.assign(off.size(), 0);
+  for (size_t i = 0; i + 1 < off.size(); ++i) {
+    first[i] = (int32_t)ch.size();
+    for (int64_t s = off[i]; s < off[i + 1]; s += kChunk) ch.push_back({s, std::min(off[i + 1], s + kChunk), (int32_t)i, 0});
+  }
+  first.back() = (int32_t)ch.size();
+}
+
+PsdArgs psd_args(strom_solver* s, const double* in, double* out, const uint8_t* act, bool admm) {
+  PsdArgs a{};
+  a.Xb = in;
+  a.out = out;
+  a.blk_off = s->blk_off.p;
+  a.blk_n = s->blk_n.p;
+  a.blk_list = s->blk_list.p;
+  a.blk_inv_sigma = admm ? s->blk_inv_sigma.p : nullptr;
+  a.blk_active = act;
+  a.lam_off = s->lam_off.p;
+  a.vscratch = s->vscratch.p;
+  return a;
+}
+
+void enqueue_iteration(strom_solver* s, cudaStream_t st) {
+  const AdmmDev& d = s->ad;
+  YsolveDev yd = s->yd;
+  yd.inst_active = s->inst_active.p;
+  admm_block_mode(d, st);
+  // Step 1: r = b/sigma - A(X/sigma + S - C), y^{k+1/2} = (A A^*)^{-1} r
+  admm_residual_rhs(d, s->S.p, s->r.p, st);
+  ysolve_apply(yd, s->ninst, s->max_group, s->r.p, s->yh.p, s->rho.p, st);
+  // Step 2: X_b = X + sigma (A^* y - C), S = (Pi(X_b) - X_b) / sigma
+  admm_xb(d, s->yh.p, s->Xb.p, st);
+  psd_launch(psd_args(s, s->Xb.p, s->S.p, s->blk_act32.p, true), s->cls, STROM_PREC_FP32, st);
+  psd_launch(psd_args(s, s->Xb.p, s->S.p, s->blk_act64.p, true), s->cls, STROM_PREC_FP64, st);
+  // Step 3: r = b/sigma - A(X/sigma + S - C), y^{k+1} = (A A^*)^{-1} r
+  admm_residual_rhs(d, s->S.p, s->r.p, st);
+  ysolve_apply(yd, s->ninst, s->max_group, s->r.p, s->y.p, s->rho.p, st);
+  // Step 4: X = X + tau sigma (S + A^* y - C), residuals, stop test, sigma rule
+  admm_xupdate(d, s->y.p, s->opt.tau, st);
+  admm_primal_res(d, s->y.p, st);
+  admm_finalize(d, s->prm, st);
+}
+
+void build_graph(strom_solver* s) {
+  if (s->graph) return;
+  psd_configure();
+  STROM_CUDA(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+  try {
+    enqueue_iteration(s, s->stream);
+  } catch (...) {
+    cudaGraph_t g;
+    cudaStreamEndCapture(s->stream, &g);
+    if (g) cudaGraphDestroy(g);
+    throw;
+  }
+  STROM_CUDA(cudaStreamEndCapture(s->stream, &s->graph_def));
+  STROM_CUDA(cudaGraphInstantiate(&s->graph, s->graph_def, 0));
+}
+
+void reset_state(strom_solver* s) {
+  s->X.zero(s->stream);
+  s->S.zero(s->stream);
+  s->y.zero(s->stream);
+  s->yh.zero(s->stream);
+  s->iters.zero(s->stream);
+  s->inst_flag.zero(s->stream);
+  s->stats.zero(s->stream);
+  std::vector<double> sg(s->ninst, s->opt.sigma0);
+  std::vector<uint8_t> one(s->ninst, 1);
+  std::vector<uint8_t> prec(s->ninst, (uint8_t)(s->opt.precision == STROM_PREC_FP64 ? STROM_PREC_FP64 : STROM_PREC_FP32));
+  STROM_CUDA(cudaMemcpyAsync(s->sigma.p, sg.data(), sizeof(double) * s->ninst, cudaMemcpyHostToDevice, s->stream));
+  STROM_CUDA(cudaMemcpyAsync(s->inst_active.p, one.data(), s->ninst, cudaMemcpyHostToDevice, s->stream));
+  STROM_CUDA(cudaMemcpyAsync(s->inst_prec.p, prec.data(), s->ninst, cudaMemcpyHostToDevice, s->stream));
+  STROM_CUDA(cudaStreamSynchronize(s->stream));
+}
+
+void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
+  s->ninst = count;
+  s->svec_off.assign(count + 1, 0);
+  s->row_off.assign(count + 1, 0);
+  for (int i = 0; i < count; ++i) {
+    const Sdp& q = *sdps[i]->s;
+    s->svec_off[i + 1] = s->svec_off[i] + q.nsvec;
+    s->row_off[i + 1] = s->row_off[i] + q.m();
+  }
+  s->nsvec = s->svec_off[count];
+  s->m = s->row_off[count];
+  if (s->nsvec > INT32_MAX || s->m > INT32_MAX) throw StatusError(STROM_ERR_INVALID, "batch too large for int32 indices");
+  // ---- concatenated host arrays
+  std::vector<int64_t> rowptr(1, 0), star_rep, star_row, oth_rows, grp_ptr(1, 0), fac_off(1, 0), coup_off(1, 0), blk_off,
+      lam_off;
+  std::vector<int32_t> col, row_inst, star_ptr, star_inst, inst_grp(1, 0), coup_n, blk_n, blk_inst;
+  std::vector<double> val, b, C, omega, inv_rep_s, star_c, star_d, star_inv_s2;
+  std::vector<int8_t> row_kind;
+  std::vector<double> normC(count);
+  s->inst_blk_off.assign(count + 1, 0);
+  int64_t lam_acc = 0;
+  for (int i = 0; i < count; ++i) {
+    const Sdp& q = *sdps[i]->s;
+    const int64_t so = s->svec_off[i], ro = s->row_off[i];
+    InstMeta mt;
+    mt.N = q.N; mt.nv = q.nv; mt.dx = q.dx; mt.du = q.du; mt.nsvec = q.nsvec; mt.m = q.m();
+    mt.block_n = q.block_n; mt.block_clique = q.block_clique; mt.block_off = q.block_off; mt.block_kind = q.block_kind;
+    mt.b = q.b;
+    s->meta.push_back(std::move(mt));
+    for (int64_t r = 0; r < q.m(); ++r) {
+      for (int64_t e = q.rowptr[r]; e < q.rowptr[r + 1]; ++e) {
+        col.push_back((int32_t)(q.col[e] + so));
+        val.push_back(q.val[e]);
+      }
+      rowptr.push_back((int64_t)val.size());
+      row_inst.push_back(i);
+    }
+    b.insert(b.end(), q.b.begin(), q.b.end());
+    C.insert(C.end(), q.C.begin(), q.C.end());
+    double nc = 0.0;
+    for (double c : q.C) nc += c * c;
+    normC[i] = std::sqrt(nc);
+    omega.insert(omega.end(), q.omega.begin(), q.omega.end());
+    inv_rep_s.insert(inv_rep_s.end(), q.inv_rep_s.begin(), q.inv_rep_s.end());
+    row_kind.insert(row_kind.end(), q.row_kind.begin(), q.row_kind.end());
+    const int32_t sp0 = (int32_t)star_row.size();
+    for (size_t c = 0; c < q.star_rep.size(); ++c) {
+      star_rep.push_back(q.star_rep[c] + so);
+      star_c.push_back(q.star_c[c]);
+      star_d.push_back(q.star_d[c]);
+      star_ptr.push_back(sp0 + q.star_ptr[c]);
+      star_inst.push_back(i);
+    }
+    for (size_t e = 0; e < q.star_row.size(); ++e) {
+      star_row.push_back(q.star_row[e] + ro);
+      star_inv_s2.push_back(q.star_inv_s2[e]);
+    }
+    const int64_t oth0 = (int64_t)oth_rows.size();
+    for (int64_t r : q.oth_rows) oth_rows.push_back(r + ro);
+    for (int k = 0; k < q.N; ++k) {
+      const int64_t mk = q.grp_ptr[k + 1] - q.grp_ptr[k];
+      grp_ptr.push_back(oth0 + q.grp_ptr[k + 1]);
+      const int cprev = (k > 0) ? q.grp_cons[k - 1] : 0;
+      coup_n.push_back(cprev);
+      fac_off.push_back(fac_off.back() + mk * mk);
+      coup_off.push_back(coup_off.back() + mk * cprev);
+      s->max_group = std::max<int>(s->max_group, (int)mk);
+    }
+    inst_grp.push_back((int32_t)(grp_ptr.size() - 1));
+    s->inst_blk_off[i] = (int64_t)blk_n.size();
+    for (size_t k = 0; k < q.block_n.size(); ++k) {
+      blk_off.push_back(q.block_off[k] + so);
+      blk_n.push_back(q.block_n[k]);
+      blk_inst.push_back(i);
+      lam_off.push_back(lam_acc);
+      lam_acc += q.block_n[k];
+    }
+  }
+  s->inst_blk_off[count] = (int64_t)blk_n.size();
+  star_ptr.push_back((int32_t)star_row.size());
+  s->nblk = (int)blk_n.size();
+  s->ngroups = (int)grp_ptr.size() - 1;
+  // ---- A^T (CSR over svec positions, rows ascending)
+  std::vector<int64_t> atptr(s->nsvec + 1, 0);
+  for (int32_t c : col) atptr[c + 1]++;
+  for (int64_t p = 0; p < s->nsvec; ++p) atptr[p + 1] += atptr[p];
+  std::vector<int32_t> atrow(col.size());
+  std::vector<double> atval(col.size());
+  {
+    std::vector<int64_t> fill(atptr.begin(), atptr.end() - 1);
+    for (int64_t r = 0; r < s->m; ++r)
+      for (int64_t e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+        const int64_t dst = fill[col[e]]++;
+        atrow[dst] = (int32_t)r;
+        atval[dst] = val[e];
+      }
+  }
+  // ---- chunks
+  std::vector<Chunk> sch, rch;
+  std::vector<int32_t> sfirst, rfirst;
+  make_chunks(s->svec_off, sch, sfirst);
+  make_chunks(s->row_off, rch, rfirst);
+  // ---- PSD classes
+  std::vector<int32_t> list;
+  build_classes(blk_n.data(), s->nblk, list, s->cls);
+  // ---- upload
+  cudaStream_t st = s->stream;
+  s->rowptr.upload(rowptr.data(), rowptr.size(), st);
+  s->col.upload(col.data(), col.size(), st);
+  s->val.upload(val.data(), val.size(), st);
+  s->atptr.upload(atptr.data(), atptr.size(), st);
+  s->atrow.upload(atrow.data(), atrow.size(), st);
+  s->atval.upload(atval.data(), atval.size(), st);
+  s->b.upload(b.data(), b.size(), st);
+  s->C.upload(C.data(), C.size(), st);
+  s->omega.upload(omega.data(), omega.size(), st);
+  s->inv_rep_s.upload(inv_rep_s.data(), inv_rep_s.size(), st);
+  s->row_kind.upload(row_kind.data(), row_kind.size(), st);
+  s->row_inst.upload(row_inst.data(), row_inst.size(), st);
+  s->star_rep.upload(star_rep.data(), star_rep.size(), st);
+  s->star_c.upload(star_c.data(), star_c.size(), st);
+  s->star_d.upload(star_d.data(), star_d.size(), st);
+  s->star_ptr.upload(star_ptr.data(), star_ptr.size(), st);
+  s->star_row.upload(star_row.data(), star_row.size(), st);
+  s->star_inv_s2.upload(star_inv_s2.data(), star_inv_s2.size(), st);
+  s->star_inst.upload(star_inst.data(), star_inst.size(), st);
+  s->oth_rows.upload(oth_rows.data(), oth_rows.size(), st);
+  s->grp_ptr.upload(grp_ptr.data(), grp_ptr.size(), st);
+  s->inst_grp.upload(inst_grp.data(), inst_grp.size(), st);
+  s->coup_n.upload(coup_n.data(), coup_n.size(), st);
+  s->fac_off.upload(fac_off.data(), fac_off.size(), st);
+  s->coup_off.upload(coup_off.data(), coup_off.size(), st);
+  s->blk_off.upload(blk_off.data(), blk_off.size(), st);
+  s->blk_n.upload(blk_n.data(), blk_n.size(), st);
+  s->blk_list.upload(list.data(), list.size(), st);
+  s->blk_inst.upload(blk_inst.data(), blk_inst.size(), st);
+  s->lam_off.upload(lam_off.data(), lam_off.size(), st);
+  s->svec_chunks.upload(sch.data(), sch.size(), st);
+  s->row_chunks.upload(rch.data(), rch.size(), st);
+  s->inst_svec_chunk.upload(sfirst.data(), sfirst.size(), st);
+  s->inst_row_chunk.upload(rfirst.data(), rfirst.size(), st);
+  s->norm_C.upload(normC.data(), normC.size(), st);
+  s->fac.alloc(std::max<int64_t>(1, fac_off.back()));
+  s->coup.alloc(std::max<int64_t>(1, coup_off.back()));
+  s->diag0.alloc(std::max<size_t>(1, oth_rows.size()));
+  s->keep.alloc(s->m);
+  STROM_CUDA(cudaMemsetAsync(s->keep.p, 1, s->m, st));
+  for (auto* v : {&s->X, &s->S, &s->Xb, &s->rho, &s->tmp_svec}) v->alloc(s->nsvec);
+  s->rho.zero(st);
+  for (auto* v : {&s->y, &s->yh, &s->r}) v->alloc(s->m);
+  s->norm_b.alloc(count);
+  s->sigma.alloc(count);
+  s->stats.alloc(8 * (size_t)count);
+  s->part_svec.alloc(2 * sch.size());
+  s->part_rows.alloc(2 * rch.size());
+  s->blk_inv_sigma.alloc(s->nblk);
+  s->inst_active.alloc(count);
+  s->inst_flag.alloc(count);
+  s->inst_prec.alloc(count);
+  s->iters.alloc(count);
+  s->n_active.alloc(1);
+  s->blk_act32.alloc(s->nblk);
+  s->blk_act64.alloc(s->nblk);
+  s->lam.alloc(std::max<int64_t>(1, lam_acc));
+  s->topvec.alloc(std::max<int64_t>(1, lam_acc));
+  if (s->cls.count[3] > 0) s->vscratch.alloc((size_t)s->cls.count[3] * 160 * 161);
+  // ---- device views
+  YsolveDev& yd = s->yd;
+  yd.rowptr = s->rowptr.p; yd.col = s->col.p; yd.val = s->val.p;
+  yd.atptr = s->atptr.p; yd.atrow = s->atrow.p; yd.atval = s->atval.p;
+  yd.row_kind = s->row_kind.p; yd.row_inst = s->row_inst.p;
+  yd.nclass = (int64_t)star_rep.size();
+  yd.star_rep = s->star_rep.p; yd.star_c = s->star_c.p; yd.star_d = s->star_d.p; yd.star_ptr = s->star_ptr.p;
+  yd.star_row = s->star_row.p; yd.star_inv_s2 = s->star_inv_s2.p; yd.star_inst = s->star_inst.p;
+  yd.omega = s->omega.p; yd.inv_rep_s = s->inv_rep_s.p;
+  yd.noth = (int64_t)oth_rows.size(); yd.oth_rows = s->oth_rows.p; yd.grp_ptr = s->grp_ptr.p;
+  yd.inst_grp = s->inst_grp.p; yd.coup_n = s->coup_n.p;
+  yd.fac = s->fac.p; yd.fac_off = s->fac_off.p; yd.coup = s->coup.p; yd.coup_off = s->coup_off.p;
+  yd.diag0 = s->diag0.p; yd.keep = s->keep.p; yd.inst_active = nullptr;
+  AdmmDev& ad = s->ad;
+  ad.ninst = count; ad.nblk = s->nblk;
+  ad.n_svec_chunks = (int)sch.size(); ad.n_row_chunks = (int)rch.size();
+  ad.svec_chunks = s->svec_chunks.p; ad.row_chunks = s->row_chunks.p;
+  ad.inst_svec_chunk = s->inst_svec_chunk.p; ad.inst_row_chunk = s->inst_row_chunk.p;
+  ad.rowptr = s->rowptr.p; ad.col = s->col.p; ad.val = s->val.p;
+  ad.atptr = s->atptr.p; ad.atrow = s->atrow.p; ad.atval = s->atval.p;
+  ad.b = s->b.p; ad.C = s->C.p; ad.keep = s->keep.p; ad.norm_b = s->norm_b.p; ad.norm_C = s->norm_C.p;
+  ad.X = s->X.p; ad.S = s->S.p; ad.sigma = s->sigma.p; ad.inst_active = s->inst_active.p;
+  ad.inst_flag = s->inst_flag.p; ad.inst_prec = s->inst_prec.p; ad.iters = s->iters.p; ad.stats = s->stats.p;
+  ad.part_svec = s->part_svec.p; ad.part_rows = s->part_rows.p; ad.n_active = s->n_active.p;
+  ad.blk_inst = s->blk_inst.p; ad.blk_act32 = s->blk_act32.p; ad.blk_act64 = s->blk_act64.p;
+  ad.blk_inv_sigma = s->blk_inv_sigma.p;
+  AdmmParams& p = s->prm;
+  p.tol = s->opt.tol; p.maxiter = s->opt.maxiter; p.sigma_every = s->opt.sigma_every;
+  p.sigma_ratio = s->opt.sigma_ratio; p.sigma_factor = s->opt.sigma_factor;
+  p.sigma_min = s->opt.sigma_min; p.sigma_max = s->opt.sigma_max;
+  p.precision = s->opt.precision; p.polish_eta = s->opt.polish_eta;
+  // ---- row reduction + factorisation (once)
+  ysolve_factor(yd, s->ngroups, count, s->opt.rank_tol, st);
+  STROM_CUDA(cudaStreamSynchronize(st));
+  std::vector<uint8_t> keep(s->m);
+  STROM_CUDA(cudaMemcpy(keep.data(), s->keep.p, s->m, cudaMemcpyDeviceToHost));
+  std::vector<double> nb(count, 0.0);
+  s->m_kept.assign(count, 0);
+  for (int i = 0; i < count; ++i) {
+    for (int64_t r = s->row_off[i]; r < s->row_off[i + 1]; ++r)
+      if (keep[r]) { nb[i] += b[r] * b[r]; s->m_kept[i]++; }
+    nb[i] = std::sqrt(nb[i]);
+  }
+  s->norm_b.upload(nb.data(), count, st);
+  reset_state(s);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" void strom_options_default(strom_options* o) {
+  if (!o) return;
+  o->tol = 1e-6;
+  o->maxiter = 50000;
+  o->sigma0 = 10.0;
+  o->tau = 1.618;
+  o->sigma_every = 20;
+  o->sigma_ratio = 5.0;
+  o->sigma_factor = 2.0;
+  o->sigma_min = 1e-4;
+  o->sigma_max = 1e4;
+  o->rank_tol = 1e-8;
+  o->precision = STROM_PREC_FP64;
+  o->polish_eta = 1e-5;
+  o->check_every = 50;
+  o->time_budget_s = 0.0;
+}
+
+extern "C" int strom_solver_create(const strom_sdp* const* sdps, int32_t count, const strom_options* opt,
+                                   strom_solver** out) {
+  return guard([&] {
+    if (!sdps || count < 1 || !out) throw StatusError(STROM_ERR_INVALID, "strom_solver_create: bad arguments");
+    for (int i = 0; i < count; ++i)
+      if (!sdps[i] || !sdps[i]->s) throw StatusError(STROM_ERR_INVALID, "strom_solver_create: null sdp");
+    std::unique_ptr<strom_solver> s(new strom_solver());
+    if (opt) s->opt = *opt;
+    else strom_options_default(&s->opt);
+    const auto& o = s->opt;
+    if (!(o.tol > 0) || o.maxiter < 1 || !(o.sigma0 > 0) || !(o.tau > 0 && o.tau < 2) || !(o.rank_tol > 0) ||
+        o.precision < 0 || o.precision > 2 || o.check_every < 1)
+      throw StatusError(STROM_ERR_INVALID, "strom_solver_create: invalid options");
+    STROM_CUDA(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+    solver_setup(s.get(), sdps, count);
+    *out = s.release();
+    return STROM_OK;
+  });
+}
+
+extern "C" void strom_solver_destroy(strom_solver* s) { delete s; }
+extern "C" int32_t strom_solver_count(const strom_solver* s) { return s ? s->ninst : 0; }
+extern "C" int64_t strom_solver_nsvec_total(const strom_solver* s) { return s ? s->nsvec : 0; }
+extern "C" int64_t strom_solver_m_total(const strom_solver* s) { return s ? s->m : 0; }
+
+extern "C" int strom_solver_offsets(const strom_solver* s, int32_t i, int64_t* so, int64_t* ro) {
+  return guard([&] {
+    if (!s || i < 0 || i >= s->ninst) throw StatusError(STROM_ERR_INVALID, "strom_solver_offsets: bad instance");
+    if (so) *so = s->svec_off[i];
+    if (ro) *ro = s->row_off[i];
+    return STROM_OK;
+  });
+}
+
+extern "C" int strom_solver_step(strom_solver* s, int32_t iters, void* stream, int32_t* n_active) {
+  return guard([&] {
+    if (!s || iters < 0) throw StatusError(STROM_ERR_INVALID, "strom_solver_step: bad arguments");
+    cudaStream_t user = (cudaStream_t)stream;
+    build_graph(s);
+    if (user) {  // order after the caller's prior work
+      cudaEvent_t ev;
+      STROM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      STROM_CUDA(cudaEventRecord(ev, user));
+      STROM_CUDA(cudaStreamWaitEvent(s->stream, ev, 0));
+      STROM_CUDA(cudaEventDestroy(ev));
+    }
+    int32_t act = 1;
+    int done = 0;
+    while (done < iters) {
+      const int n = std::min(iters - done, s->opt.check_every);
+      for (int k = 0; k < n; ++k) STROM_CUDA(cudaGraphLaunch(s->graph, s->stream));
+      done += n;
+      STROM_CUDA(cudaMemcpyAsync(&act, s->n_active.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+      STROM_CUDA(cudaStreamSynchronize(s->stream));
+      if (act == 0) break;
+    }
+    if (user) {
+      cudaEvent_t ev;
+      STROM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      STROM_CUDA(cudaEventRecord(ev, s->stream));
+      STROM_CUDA(cudaStreamWaitEvent(user, ev, 0));
+      STROM_CUDA(cudaEventDestroy(ev));
+    }
+    if (n_active) *n_active = act;
+    return STROM_OK;
+  });
+}
+
+extern "C" int strom_solve(strom_solver* s, void* stream) {
+  int32_t act = 1;
+  int st = strom_solver_step(s, s ? s->opt.maxiter : 0, stream, &act);
+  if (st != STROM_OK) return st;
+  std::vector<uint8_t> flag(s->ninst);
+  if (cudaMemcpy(flag.data(), s->inst_flag.p, s->ninst, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    set_error("strom_solve: copy of the instance flags failed");
+    return STROM_ERR_CUDA;
+  }
+  for (uint8_t f : flag)
+    if (f == 2) { set_error("strom_solve: NaN or Inf in an instance"); return STROM_ERR_NUMERICAL; }
+  for (uint8_t f : flag)
+    if (f != 1) return STROM_MAXITER;
+  return STROM_OK;
+}
+
+extern "C" int strom_solver_reset(strom_solver* s, int32_t i, const double* X0, const double* S0, double sigma) {
+  return guard([&] {
+    if (!s || i < -1 || i >= s->ninst) throw StatusError(STROM_ERR_INVALID, "strom_solver_reset: bad instance");
+    if (i == -1) {
+      reset_state(s);
+      return STROM_OK;
+    }
+    const int64_t so = s->svec_off[i], n = s->svec_off[i + 1] - so;
+    const int64_t ro = s->row_off[i], m = s->row_off[i + 1] - ro;
+    cudaStream_t st = s->stream;
+    if (X0) STROM_CUDA(cudaMemcpyAsync(s->X.p + so, X0, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    else STROM_CUDA(cudaMemsetAsync(s->X.p + so, 0, n * sizeof(double), st));
+    if (S0) STROM_CUDA(cudaMemcpyAsync(s->S.p + so, S0, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    else STROM_CUDA(cudaMemsetAsync(s->S.p + so, 0, n * sizeof(double), st));
+    STROM_CUDA(cudaMemsetAsync(s->y.p + ro, 0, m * sizeof(double), st));
+    const double sg = sigma > 0 ? sigma : s->opt.sigma0;
+    const uint8_t one = 1, zero = 0;
+    const uint8_t prec = (uint8_t)(s->opt.precision == STROM_PREC_FP64 ? STROM_PREC_FP64 : STROM_PREC_FP32);
+    const int32_t zi = 0;
+    STROM_CUDA(cudaMemcpyAsync(s->sigma.p + i, &sg, sizeof(double), cudaMemcpyHostToDevice, st));
+    STROM_CUDA(cudaMemcpyAsync(s->inst_active.p + i, &one, 1, cudaMemcpyHostToDevice, st));
+    STROM_CUDA(cudaMemcpyAsync(s->inst_flag.p + i, &zero, 1, cudaMemcpyHostToDevice, st));
+    STROM_CUDA(cudaMemcpyAsync(s->inst_prec.p + i, &prec, 1, cudaMemcpyHostToDevice, st));
+    STROM_CUDA(cudaMemcpyAsync(s->iters.p + i, &zi, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    STROM_CUDA(cudaStreamSynchronize(st));
+    return STROM_OK;
+  });
+}
+
+extern "C" int strom_get_result(const strom_solver* s, int32_t i, strom_result* r) {
+  return guard([&] {
+    if (!s || !r || i < 0 || i >= s->ninst) throw StatusError(STROM_ERR_INVALID, "strom_get_result: bad arguments");
+    double st[8];
+    int32_t it;
+    uint8_t flag;
+    double sg;
+    STROM_CUDA(cudaMemcpy(st, s->stats.p + 8 * (int64_t)i, sizeof(st), cudaMemcpyDeviceToHost));
+    STROM_CUDA(cudaMemcpy(&it, s->iters.p + i, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    STROM_CUDA(cudaMemcpy(&flag, s->inst_flag.p + i, 1, cudaMemcpyDeviceToHost));
+    STROM_CUDA(cudaMemcpy(&sg, s->sigma.p + i, sizeof(double), cudaMemcpyDeviceToHost));
+    r->status = flag == 1 ? STROM_OK : flag == 2 ? STROM_ERR_NUMERICAL : STROM_MAXITER;
+    r->iterations = it;
+    r->eta_p = st[0]; r->eta_d = st[1]; r->eta_g = st[2]; r->pobj = st[3]; r->dobj = st[4];
+    r->sigma = sg;
+    r->m_kept = s->m_kept[i];
+    return STROM_OK;
+  });
+}
+
+extern "C" int strom_get_state(const strom_solver* s, int32_t i, double* X, double* S, double* y) {
+  return guard([&] {
+    if (!s || i < 0 || i >= s->ninst) throw StatusError(STROM_ERR_INVALID, "strom_get_state: bad instance");
+    const int64_t so = s->svec_off[i], n = s->svec_off[i + 1] - so;
+    const int64_t ro = s->row_off[i], m = s->row_off[i + 1] - ro;
+    if (X) STROM_CUDA(cudaMemcpy(X, s->X.p + so, n * sizeof(double), cudaMemcpyDeviceToHost));
+    if (S) STROM_CUDA(cudaMemcpy(S, s->S.p + so, n * sizeof(double), cudaMemcpyDeviceToHost));
+    if (y) STROM_CUDA(cudaMemcpy(y, s->y.p + ro, m * sizeof(double), cudaMemcpyDeviceToHost));
+    return STROM_OK;
+  });
+}
+
+extern "C" int strom_get_kept_rows(const strom_solver* s, int32_t i, uint8_t* keep) {
+  return guard([&] {
+    if (!s || !keep || i < 0 || i >= s->ninst) throw StatusError(STROM_ERR_INVALID, "strom_get_kept_rows: bad arguments");
+    const int64_t ro = s->row_off[i], m = s->row_off[i + 1] - ro;
+    STROM_CUDA(cudaMemcpy(keep, s->keep.p + ro, m, cudaMemcpyDeviceToHost));
+    return STROM_OK;
+  });
+}
+
+extern "C" int strom_get_moment(const strom_solver* s, int32_t i, int32_t k, double* Mk) {
+  return guard([&] {
+    if (!s || !Mk || i < 0 || i >= s->ninst) throw StatusError(STROM_ERR_INVALID, "strom_get_moment: bad arguments");
+    const InstMeta& mt = s->meta[i];
+    int blk = -1;
+    for (size_t b = 0; b < mt.block_n.size(); ++b)
+      if (mt.block_kind[b] == 0 && mt.block_clique[b] == k) blk = (int)b;
+    if (blk < 0) throw StatusError(STROM_ERR_INVALID, "strom_get_moment: no such clique");
+    const int n = mt.block_n[blk];
+    std::vector<double> v((size_t)n * (n + 1) / 2);
+    STROM_CUDA(cudaMemcpy(v.data(), s->X.p + s->svec_off[i] + mt.block_off[blk], v.size() * sizeof(double),
+                          cudaMemcpyDeviceToHost));
+    for (int j = 0; j < n; ++j)
+      for (int q = 0; q <= j; ++q) {
+        const double x = v[(size_t)j * (j + 1) / 2 + q] * (q == j ? 1.0 : 0.70710678118654752440);
+        Mk[(size_t)j * n + q] = x;
+        Mk[(size_t)q * n + j] = x;
+      }
+    return STROM_OK;
+  });
+}
+
+extern "C" int strom_kernel_A(const strom_solver* s, const double* x_dev, double* Ax_dev, void* stream) {
+  return guard([&] {
+    if (!s || !x_dev || !Ax_dev) throw StatusError(STROM_ERR_INVALID, "strom_kernel_A: bad arguments");
+    csr_spmv(s->rowptr.p, s->col.p, s->val.p, s->m, x_dev, Ax_dev, (cudaStream_t)stream);
+    return STROM_OK;
+  });
+}
+
+extern "C" int strom_kernel_At(const strom_solver* s, const double* y_dev, double* x_dev, void* stream) {
+  return guard([&] {
+    if (!s || !x_dev || !y_dev) throw StatusError(STROM_ERR_INVALID, "strom_kernel_At: bad arguments");
+    csr_spmv(s->atptr.p, s->atrow.p, s->atval.p, s->nsvec, y_dev, x_dev, (cudaStream_t)stream);
+    return STROM_OK;
+  });
+}
+
+extern "C" int strom_kernel_solve(const strom_solver* s, const double* r_dev, double* y_dev, void* stream) {
+  return guard([&] {
+    if (!s || !r_dev || !y_dev || r_dev == y_dev) throw StatusError(STROM_ERR_INVALID, "strom_kernel_solve: bad arguments");
+    YsolveDev yd = s->yd;
+    yd.inst_active = nullptr;
+    ysolve_apply(yd, s->ninst, s->max_group, r_dev, y_dev, const_cast<double*>(s->rho.p), (cudaStream_t)stream);
+    return STROM_OK;
+  });
+}
+
+// helpers for the certificate (certify.cpp)
+namespace strom {
+struct CertDevice {
+  const strom_solver* s;
+};
+void solver_eig_blocks(strom_solver* s, int inst, bool use_Z, std::vector<double>& lam, std::vector<double>& topvec);
+}  // namespace strom
+
+namespace {
+__global__ void z_kernel(const int64_t* atptr, const int32_t* atrow, const double* atval, const double* y, const double* C,
+                         int64_t begin, int64_t end, double* Z) {
+  const int64_t p = begin + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= end) return;
+  double acc = 0.0;
+  for (int64_t e = atptr[p]; e < atptr[p + 1]; ++e) acc += atval[e] * y[atrow[e]];
+  Z[p] = C[p] - acc;
+}
+}  // namespace
+
+// eigenvalues (ascending, per block) and top eigenvectors of instance `inst`
+// for X (use_Z = false) or Z = C - A^T y (use_Z = true); FP64 Jacobi on the GPU
+void strom::solver_eig_blocks(strom_solver* s, int inst, bool use_Z, std::vector<double>& lam, std::vector<double>& topvec) {
+  const int64_t so = s->svec_off[inst], se = s->svec_off[inst + 1];
+  const double* in = s->X.p;
+  if (use_Z) {
+    z_kernel<<<ceil_div(se - so, 256), 256, 0, s->stream>>>(s->atptr.p, s->atrow.p, s->atval.p, s->y.p, s->C.p, so, se,
+                                                          s->tmp_svec.p);
+    STROM_CUDA(cudaGetLastError());
+    in = s->tmp_svec.p;
+  }
+  // a block list with only this instance's blocks
+  const int b0 = (int)s->inst_blk_off[inst], b1 = (int)s->inst_blk_off[inst + 1];
+  std::vector<int32_t> bn(b1 - b0), ids;
+  std::vector<int32_t> nall(s->nblk);
+  STROM_CUDA(cudaMemcpy(nall.data(), s->blk_n.p, sizeof(int32_t) * s->nblk, cudaMemcpyDeviceToHost));
+  PsdClasses cls;
+  std::vector<std::vector<int32_t>> per(4);
+  for (int b = b0; b < b1; ++b) {
+    const int n = nall[b];
+    per[n <= 16 ? 0 : n <= 40 ? 1 : n <= 80 ? 2 : 3].push_back(b);
+  }
+  for (int k = 0; k < 4; ++k) {
+    cls.start[k] = (int)ids.size();
+    cls.count[k] = (int)per[k].size();
+    for (int b : per[k]) ids.push_back(b);
+  }
+  DevBuf<int32_t> list;
+  list.upload(ids.data(), ids.size(), s->stream);
+  DevBuf<double> vs;
+  if (cls.count[3] > 0) vs.alloc((size_t)cls.count[3] * 160 * 161);
+  PsdArgs a{};
+  a.Xb = in;
+  a.out = nullptr;
+  a.blk_off = s->blk_off.p;
+  a.blk_n = s->blk_n.p;
+  a.blk_list = list.p;
+  a.lam = s->lam.p;
+  a.lam_off = s->lam_off.p;
+  a.topvec = s->topvec.p;
+  a.vscratch = vs.p;
+  psd_launch(a, cls, STROM_PREC_FP64, s->stream);
+  STROM_CUDA(cudaStreamSynchronize(s->stream));
+  lam.assign(s->lam.n, 0.0);
+  topvec.assign(s->topvec.n, 0.0);
+  STROM_CUDA(cudaMemcpy(lam.data(), s->lam.p, sizeof(double) * lam.size(), cudaMemcpyDeviceToHost));
+  STROM_CUDA(cudaMemcpy(topvec.data(), s->topvec.p, sizeof(double) * topvec.size(), cudaMemcpyDeviceToHost));
+}
+
+namespace strom {
+int solver_blocks_of(const strom_solver* s, int inst, std::vector<int32_t>& n, std::vector<int8_t>& kind,
+                     std::vector<int32_t>& clique, std::vector<int64_t>& lam_off, double* by) {
+  const InstMeta& mt = s->meta[inst];
+  n = mt.block_n;
+  kind = mt.block_kind;
+  clique = mt.block_clique;
+  lam_off.clear();
+  std::vector<int64_t> all(s->nblk);
+  STROM_CUDA(cudaMemcpy(all.data(), s->lam_off.p, sizeof(int64_t) * s->nblk, cudaMemcpyDeviceToHost));
+  for (int64_t b = s->inst_blk_off[inst]; b < s->inst_blk_off[inst + 1]; ++b) lam_off.push_back(all[b]);
+  double st[8];
+  STROM_CUDA(cudaMemcpy(st, s->stats.p + 8 * (int64_t)inst, sizeof(st), cudaMemcpyDeviceToHost));
+  // <b, y> over kept rows of this instance, recomputed from the current y
+  const int64_t ro = s->row_off[inst], m = s->row_off[inst + 1] - ro;
+  std::vector<double> y(m);
+  std::vector<uint8_t> keep(m);
+  STROM_CUDA(cudaMemcpy(y.data(), s->y.p + ro, m * sizeof(double), cudaMemcpyDeviceToHost));
+  STROM_CUDA(cudaMemcpy(keep.data(), s->keep.p + ro, m, cudaMemcpyDeviceToHost));
+  double acc = 0.0;
+  for (int64_t r = 0; r < m; ++r)
+    if (keep[r]) acc += mt.b[r] * y[r];
+  *by = acc;
+  return mt.N;
+}
+}  // namespace strom

@@ -1,0 +1,76 @@
+"""A(X), A^T(y), row reduction and the y-solve vs the oracle (FP64)."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import relax as OR
+from oracle import sgs_admm as OA
+
+from gpu_common import dev, host, lib, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(S, problems, **opt):
+    sdps = [S.Problem(p).relax() for p in problems]
+    return S.Solver(sdps, **opt), [OR.relax(p) for p in problems]
+
+
+@pytest.fixture(scope="module")
+def pend_batch():
+    S = lib()
+    probs = [wl.pendulum_problem(N=10, theta0=t) for t in (0.1, -0.17, 0.02)]
+    solver, osdps = _batch(S, probs)
+    return S, probs, solver, osdps
+
+
+def test_A_and_At(pend_batch):
+    S, probs, solver, osdps = pend_batch
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal(solver.nsvec_total)
+    y = rng.standard_normal(solver.m_total)
+    xd, yd = dev(x), dev(y)
+    ax = torch.zeros(solver.m_total, dtype=torch.float64, device="cuda:0")
+    aty = torch.zeros(solver.nsvec_total, dtype=torch.float64, device="cuda:0")
+    solver.kernel_A(xd.data_ptr(), ax.data_ptr())
+    solver.kernel_At(yd.data_ptr(), aty.data_ptr())
+    ax, aty = host(ax), host(aty)
+    for i, o in enumerate(osdps):
+        so, ro = solver.offsets(i)
+        want = o.A @ x[so:so + o.nsvec]
+        assert np.max(np.abs(ax[ro:ro + o.m] - want)) <= 1e-13 * np.max(np.abs(want))
+        want_t = o.A.T @ y[ro:ro + o.m]
+        assert np.max(np.abs(aty[so:so + o.nsvec] - want_t)) <= 1e-13 * np.max(np.abs(want_t))
+
+
+@pytest.mark.parametrize("which", ["pendulum", "toy", "cartpole"])
+def test_row_reduction_matches_oracle(which):
+    S = lib()
+    if which == "pendulum":
+        probs = [wl.pendulum_problem(N=10, theta0=0.1), wl.pendulum_problem(N=4, theta0=-0.05)]
+    elif which == "toy":
+        probs = [wl.toy_problem(N=3), wl.toy_problem(N=5)]
+    else:
+        probs = [wl.cartpole_problem(N=2, x0=0.1, theta0=0.2)]
+    solver, osdps = _batch(S, probs)
+    for i, o in enumerate(osdps):
+        keep, _ = OA.reduce_rows(o)
+        assert np.array_equal(solver.kept_rows(i), keep)
+
+
+def test_ysolve_matches_oracle(pend_batch):
+    S, probs, solver, osdps = pend_batch
+    rng = np.random.default_rng(2)
+    r = rng.standard_normal(solver.m_total)
+    rd = dev(r)
+    yd = torch.zeros_like(rd)
+    solver.kernel_solve(rd.data_ptr(), yd.data_ptr())
+    y = host(yd)
+    for i, o in enumerate(osdps):
+        red = OA.reduce(o)
+        so, ro = solver.offsets(i)
+        want = OA.YSolver(red.A)(r[ro:ro + o.m][red.keep])
+        got = y[ro:ro + o.m]
+        assert np.all(got[~red.keep] == 0.0)
+        err = np.linalg.norm(got[red.keep] - want) / np.linalg.norm(want)
+        assert err <= 1e-10, err

@@ -1,0 +1,96 @@
+"""Whole sGS-ADMM solves on the GPU vs the FP64 oracle (Algorithm 1)."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import certify as OC
+from oracle import relax as OR
+from oracle import sgs_admm as OA
+
+from gpu_common import lib
+
+pytestmark = pytest.mark.gpu
+
+_REF = {}
+
+
+def oracle_ref(p, key):
+    """Oracle run to eta <= 1e-8; parity of the objective is judged against it."""
+    if key not in _REF:
+        red = OA.reduce(OR.relax(p))
+        res = OA.solve(red, OA.Options(tol=1e-8, maxiter=60000))
+        _REF[key] = (red, res)
+    return _REF[key]
+
+
+def test_pendulum_fp64_matches_oracle():
+    S = lib()
+    p = wl.pendulum_problem(N=10, theta0=0.1)
+    solver = S.Solver([S.Problem(p).relax()], tol=1e-6, precision=S.STROM_PREC_FP64)
+    assert solver.solve() == S.STROM_OK
+    r = solver.result(0)
+    assert max(r.eta_p, r.eta_d, r.eta_g) <= 1e-6
+    red, ref = oracle_ref(p, ("pend10", 0.1))
+    assert ref.converged
+    assert abs(r.pobj - ref.pobj) / (1 + abs(ref.pobj)) <= 1e-6
+    assert r.m_kept == red.keep.sum()
+
+
+def test_first_iterations_match_oracle():
+    """The first iterates agree with Algorithm 1 run by the oracle (same sigma schedule)."""
+    S = lib()
+    p = wl.pendulum_problem(N=6, theta0=-0.07)
+    solver = S.Solver([S.Problem(p).relax()], tol=1e-12, maxiter=30, check_every=1,
+                      precision=S.STROM_PREC_FP64)
+    solver.step(30)
+    X, Sg, y = solver.state(0)
+    red = OA.reduce(OR.relax(p))
+    ref = OA.solve(red, OA.Options(tol=1e-12, maxiter=30))
+    assert np.linalg.norm(X - ref.X) <= 1e-9 * np.linalg.norm(ref.X)
+    assert np.linalg.norm(Sg - ref.S) <= 1e-9 * max(1.0, np.linalg.norm(ref.S))
+    yk = np.zeros(red.sdp.m)
+    yk[red.keep] = ref.y
+    # y = (A A^T)^{-1} r carries the conditioning of A A^T on top of the iterate error
+    assert np.linalg.norm(y - yk) <= 1e-8 * np.linalg.norm(yk)
+
+
+def test_batch_equals_alone():
+    S = lib()
+    probs = [wl.pendulum_problem(N=10, theta0=t) for t in (0.1, -0.17, 0.19)]
+    sdps = [S.Problem(p).relax() for p in probs]
+    batch = S.Solver(sdps, tol=1e-6, precision=S.STROM_PREC_FP64)
+    batch.solve()
+    for i, p in enumerate(probs):
+        alone = S.Solver([S.Problem(p).relax()], tol=1e-6, precision=S.STROM_PREC_FP64)
+        alone.solve()
+        a, b = alone.result(0), batch.result(i)
+        assert a.iterations == b.iterations
+        assert a.pobj == b.pobj and a.dobj == b.dobj
+
+
+def test_mixed_precision_matches_fp64():
+    S = lib()
+    p = wl.pendulum_problem(N=10, theta0=0.1)
+    solver = S.Solver([S.Problem(p).relax()], tol=1e-6, precision=S.STROM_PREC_MIXED, polish_eta=1e-5)
+    assert solver.solve() == S.STROM_OK
+    r = solver.result(0)
+    _, ref = oracle_ref(p, ("pend10", 0.1))
+    assert max(r.eta_p, r.eta_d, r.eta_g) <= 1e-6
+    assert abs(r.pobj - ref.pobj) / (1 + abs(ref.pobj)) <= 1e-6
+
+
+def test_certificate_matches_oracle():
+    S = lib()
+    p = wl.pendulum_problem(N=10, theta0=0.1)
+    P = S.Problem(p)
+    solver = S.Solver([P.relax()], tol=1e-6, precision=S.STROM_PREC_FP64)
+    solver.solve()
+    c = solver.certify(0, P)
+    red, _ = oracle_ref(p, ("pend10", 0.1))
+    X, _, y = solver.state(0)
+    oc = OC.certify(p, red, X, y[red.keep])
+    assert c.rank_one == oc.rank_one and c.certified == oc.certified and c.feasible == oc.feasible
+    assert abs(c.lower_bound - oc.lower_bound) <= 1e-9 * (1 + abs(oc.lower_bound))
+    assert abs(c.phat - oc.phat) <= 1e-9 * (1 + abs(oc.phat))
+    assert c.xi >= -1e-12
+    assert c.lower_bound <= c.phat + 1e-9

@@ -1,0 +1,77 @@
+"""The C ABI library loads, exports every declared symbol, validates input,
+and its host relaxation builder reproduces the oracle's SDP exactly (CPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import relax as OR
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2406_05846_gb300 import build
+    build.build()
+    import paper_2406_05846_gb300 as pkg
+    pkg.lib()
+    return pkg
+
+
+def test_exports_every_declared_symbol(S):
+    hdr = open(os.path.join(ROOT, "include", "strom.h")).read()
+    names = set(re.findall(r"^[a-z_0-9 \*]*?\b(strom_[A-Za-z_0-9]+)\s*\(", hdr, flags=re.M))
+    assert len(names) > 25
+    L = ctypes.CDLL(os.path.join(ROOT, "paper_2406_05846_gb300", "libstrom.so"))
+    missing = [n for n in sorted(names) if not hasattr(L, n)]
+    assert not missing, missing
+    from paper_2406_05846_gb300 import _native
+    assert names == set(_native.SIGNATURES), names ^ set(_native.SIGNATURES)
+
+
+@pytest.mark.parametrize("which", ["toy", "pendulum", "cartpole", "rigid"])
+def test_builder_matches_oracle(S, which):
+    if which == "toy":
+        p = wl.toy_problem(N=3)
+    elif which == "pendulum":
+        p = wl.pendulum_problem(N=5, theta0=0.13)
+    elif which == "cartpole":
+        p = wl.cartpole_problem(N=2, x0=0.2, theta0=0.1)
+    else:
+        p = wl.rigid_body_problem(N=2, disks=[(0.5, -0.3, 0.4), (-1.0, 1.0, 0.6)])
+    a = S.Problem(p).relax().export()
+    o = OR.relax(p)
+    assert np.array_equal(a.block_n, [b.n for b in o.blocks])
+    assert np.array_equal(a.block_off, [b.offset for b in o.blocks])
+    assert np.array_equal(a.rowptr, o.A.indptr)
+    assert np.array_equal(a.col, o.A.indices)
+    assert np.max(np.abs(a.val - o.A.data)) <= 1e-15 * np.max(np.abs(o.A.data))
+    assert np.max(np.abs(a.C - o.C)) <= 1e-15 * max(1.0, np.max(np.abs(o.C)))
+    assert np.array_equal(a.b, o.b)
+    assert np.array_equal(a.row_kind, o.row_kind)
+    assert np.array_equal(a.row_clique, o.row_clique)
+
+
+def test_problem_validation(S):
+    p = wl.toy_problem(N=2)
+    p.kappa = 3
+    with pytest.raises(RuntimeError, match="kappa"):
+        S.Problem(p)
+    p = wl.toy_problem(N=2)
+    p.cliques[0].g.append(wl.Poly.var(3, 0) ** 3)   # cubic inequality: degree too high
+    with pytest.raises(RuntimeError, match="degree"):
+        S.Problem(p)
+
+
+def test_no_gpu_no_fallback(S):
+    """Without a GPU the solver must fail loudly instead of computing on the CPU."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    sdp = S.Problem(wl.toy_problem(N=2)).relax()
+    with pytest.raises(RuntimeError):
+        S.Solver([sdp])
