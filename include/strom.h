@@ -151,6 +151,12 @@ int strom_solver_create(const strom_sdp* const* sdps, int32_t count, const strom
 void strom_solver_destroy(strom_solver* s);
 int32_t strom_solver_count(const strom_solver* s);
 
+/* Recomputes the row reduction and the factorisation of A A^T from the data
+ * already on the device and resets every instance to X = S = y = 0,
+ * sigma = sigma0 (the setup of Sec. 4, repeated; used to time a whole solve
+ * with inputs resident in HBM). */
+int strom_solver_factor(strom_solver* s, void* stream);
+
 /* Runs Algorithm 1 until every instance meets tol or maxiter. Returns
  * STROM_OK when all converged, STROM_MAXITER otherwise. */
 int strom_solve(strom_solver* s, void* stream);
@@ -191,6 +197,18 @@ typedef struct {
 /* zbar, zhat: optional host outputs of length N (dx + du) + dx. */
 int strom_certify(strom_solver* s, int32_t i, const strom_problem* p, double rank_tol, double xi_tol,
                   strom_certificate* out, double* zbar, double* zhat);
+
+/* The certificate of every instance of the solver; problems[i] describes
+ * instance i. out: [count]. Eigenvalues of all blocks are computed in two
+ * batched GPU launches; the rollout and bound run on the host. */
+int strom_certify_batch(strom_solver* s, const strom_problem* const* problems, double rank_tol, double xi_tol,
+                        strom_certificate* out);
+
+/* Number of CUDA kernels libstrom has launched in this process (a graph
+ * launch counts each of its kernel nodes). */
+uint64_t strom_launch_count(void);
+/* Bytes libstrom has copied host->device and device->host in this process. */
+void strom_transfer_bytes(uint64_t* h2d, uint64_t* d2h);
 
 /* ------------------------------------------------------------------------
  * Kernel-level entry points for parity tests (device pointers, caller's

@@ -72,6 +72,10 @@ SIGNATURES = {
     "strom_solver_destroy": (None, [P]),
     "strom_solver_count": (C.c_int32, [P]),
     "strom_solve": (C.c_int, [P, P]),
+    "strom_solver_factor": (C.c_int, [P, P]),
+    "strom_certify_batch": (C.c_int, [P, C.POINTER(P), C.c_double, C.c_double, C.POINTER(strom_certificate)]),
+    "strom_launch_count": (C.c_uint64, []),
+    "strom_transfer_bytes": (None, [C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     "strom_solver_step": (C.c_int, [P, C.c_int32, P, PI32]),
     "strom_solver_reset": (C.c_int, [P, C.c_int32, PD, PD, C.c_double]),
     "strom_get_result": (C.c_int, [P, C.c_int32, C.POINTER(strom_result)]),

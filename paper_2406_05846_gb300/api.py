@@ -167,6 +167,18 @@ class Solver:
     def __len__(self):
         return lib().strom_solver_count(self.handle)
 
+    def factor(self, stream=None):
+        """Row reduction + factorisation from device-resident data, fresh state."""
+        check(lib().strom_solver_factor(self.handle, stream), "strom_solver_factor")
+
+    def certify_batch(self, problems, rank_tol=1e-4, xi_tol=1e-2):
+        n = len(self)
+        arr = (C.c_void_p * n)(*[pr.handle.value for pr in problems])
+        out = (N.strom_certificate * n)()
+        check(lib().strom_certify_batch(self.handle, arr, rank_tol, xi_tol, out), "strom_certify_batch")
+        return [Certificate(c.max_ratio, c.lower_bound, c.phat, c.xi, c.hmax, c.gmin, bool(c.feasible),
+                            bool(c.rank_one), bool(c.certified), None, None) for c in out]
+
     def solve(self, stream=None) -> int:
         return check(lib().strom_solve(self.handle, stream), "strom_solve")
 
@@ -255,6 +267,18 @@ class PsdPlan:
 
     def execute(self, xb_ptr, out_ptr, lam_ptr=None, stream=None):
         check(lib().strom_psd_execute(self.handle, xb_ptr, out_ptr, lam_ptr, stream), "strom_psd_execute")
+
+
+def launch_count() -> int:
+    """Kernels launched by libstrom in this process (graph nodes counted per replay)."""
+    return int(lib().strom_launch_count())
+
+
+def transfer_bytes():
+    """(host->device, device->host) bytes copied by libstrom in this process."""
+    h, d = C.c_uint64(), C.c_uint64()
+    lib().strom_transfer_bytes(C.byref(h), C.byref(d))
+    return int(h.value), int(d.value)
 
 
 def kernel_psd_project(xb_ptr, blk_off, blk_n, precision, out_ptr, stream=None):

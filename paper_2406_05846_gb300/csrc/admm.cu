@@ -195,32 +195,39 @@ __global__ void spmv_kernel(const int64_t* __restrict__ ptr, const int32_t* __re
 void admm_residual_rhs(const AdmmDev& d, const double* S, double* r, cudaStream_t st) {
   residual_rhs_kernel<<<d.n_row_chunks, CT, 0, st>>>(d, S, r);
   STROM_CUDA(cudaGetLastError());
+  count_launches(1);
 }
 void admm_xb(const AdmmDev& d, const double* y, double* Xb, cudaStream_t st) {
   xb_kernel<<<d.n_svec_chunks, CT, 0, st>>>(d, y, Xb);
   STROM_CUDA(cudaGetLastError());
+  count_launches(1);
 }
 void admm_xupdate(const AdmmDev& d, const double* y, double tau, cudaStream_t st) {
   xupdate_kernel<<<d.n_svec_chunks, CT, 0, st>>>(d, y, tau);
   STROM_CUDA(cudaGetLastError());
+  count_launches(1);
 }
 void admm_primal_res(const AdmmDev& d, const double* y, cudaStream_t st) {
   primal_res_kernel<<<d.n_row_chunks, CT, 0, st>>>(d, y);
   STROM_CUDA(cudaGetLastError());
+  count_launches(1);
 }
 void admm_finalize(const AdmmDev& d, const AdmmParams& p, cudaStream_t st) {
   finalize_kernel<<<1, 1024, 0, st>>>(d, p);
   STROM_CUDA(cudaGetLastError());
+  count_launches(1);
 }
 void admm_block_mode(const AdmmDev& d, cudaStream_t st) {
   block_mode_kernel<<<ceil_div(d.nblk, 256), 256, 0, st>>>(d);
   STROM_CUDA(cudaGetLastError());
+  count_launches(1);
 }
 void csr_spmv(const int64_t* ptr, const int32_t* idx, const double* val, int64_t nrows, const double* x,
               double* out, cudaStream_t st) {
   if (nrows == 0) return;
   spmv_kernel<<<ceil_div(nrows, 256), 256, 0, st>>>(ptr, idx, val, nrows, x, out);
   STROM_CUDA(cudaGetLastError());
+  count_launches(1);
 }
 
 }  // namespace strom

@@ -1,4 +1,5 @@
 // C ABI: errors, problem descriptions and the relaxation builder.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -9,11 +10,22 @@
 
 namespace {
 thread_local std::string g_err;
-}
+std::atomic<uint64_t> g_launches{0};
+std::atomic<uint64_t> g_h2d{0}, g_d2h{0};
+}  // namespace
 
 namespace strom {
 void set_error(const std::string& msg) { g_err = msg; }
+void count_launches(int64_t n) { g_launches.fetch_add((uint64_t)n); }
+void count_h2d(uint64_t b) { g_h2d.fetch_add(b); }
+void count_d2h(uint64_t b) { g_d2h.fetch_add(b); }
 }  // namespace strom
+
+extern "C" uint64_t strom_launch_count(void) { return g_launches.load(); }
+extern "C" void strom_transfer_bytes(uint64_t* h2d, uint64_t* d2h) {
+  if (h2d) *h2d = g_h2d.load();
+  if (d2h) *d2h = g_d2h.load();
+}
 
 using namespace strom;
 

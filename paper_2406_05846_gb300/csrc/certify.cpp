@@ -17,6 +17,10 @@
 
 namespace strom {
 void solver_eig_blocks(strom_solver* s, int inst, bool use_Z, std::vector<double>& lam, std::vector<double>& topvec);
+void solver_eig_all(strom_solver* s, bool use_Z, std::vector<double>& lam, std::vector<double>& topvec,
+                    std::vector<int64_t>& lam_off, std::vector<double>& stats);
+int solver_inst_blocks(const strom_solver* s, int inst, std::vector<int32_t>& n, std::vector<int8_t>& kind,
+                       std::vector<int32_t>& clique, int64_t* first_blk);
 int solver_blocks_of(const strom_solver* s, int inst, std::vector<int32_t>& n, std::vector<int8_t>& kind,
                      std::vector<int32_t>& clique, std::vector<int64_t>& lam_off, double* by);
 
@@ -130,6 +134,78 @@ std::vector<double> rollout(const Problem& p, const std::vector<double>& zbar) {
   return z;
 }
 
+namespace {
+
+// certificate of one instance from the eigen data of its blocks
+// (lamX/topX: eigenvalues ascending and top eigenvector of X's blocks,
+// lamZ: eigenvalues of Z = C - A^T y; lo[b]: offset of block b in them)
+void certify_one(const Problem& p, const std::vector<int32_t>& bn, const std::vector<int8_t>& bk,
+                 const std::vector<int32_t>& bc, const int64_t* lo, const double* lamX, const double* topX,
+                 const double* lamZ, double by, double rank_tol, double xi_tol, strom_certificate* out,
+                 double* zbar_out, double* zhat_out) {
+  const int nv = p.nv(), dx = p.dx, du = p.du;
+  std::vector<double> zbar(p.nz(), 0.0);
+  double max_ratio = 0.0;
+  for (size_t b = 0; b < bn.size(); ++b) {
+    if (bk[b] != 0) continue;
+    const int n = bn[b];
+    const double l1 = lamX[lo[b] + n - 1], l2 = lamX[lo[b] + n - 2];
+    const double ratio = l1 > 0 ? l2 / l1 : INFINITY;
+    max_ratio = std::max(max_ratio, ratio);
+    const double v0 = topX[lo[b]];
+    const int k = bc[b];
+    const int s0 = k * (dx + du);
+    for (int t = 0; t < dx + du; ++t) zbar[s0 + t] = topX[lo[b] + 1 + t] / v0;
+    if (k == p.N - 1)
+      for (int t = dx + du; t < nv; ++t) zbar[s0 + t] = topX[lo[b] + 1 + t] / v0;
+  }
+  std::vector<double> zhat = rollout(p, zbar);
+  double hmax = 0.0, gmin = INFINITY, phat = 0.0;
+  for (int k = 0; k < p.N; ++k) {
+    const double* zk = zhat.data() + k * (dx + du);
+    for (auto& h : p.cl[k].h) hmax = std::max(hmax, std::fabs(peval(h, nv, zk)));
+    for (auto& g : p.cl[k].g) gmin = std::min(gmin, peval(g, nv, zk));
+    phat += peval(p.cl[k].f, nv, zk);
+  }
+  const double feas_tol = 1e-9;
+  const bool feasible = hmax <= feas_tol && gmin >= -feas_tol;
+  const double R = std::max(1.0, p.R);
+  const int kappa = p.kappa;
+  double lb = by;
+  std::vector<int> gi(p.N, 0);
+  for (size_t b = 0; b < bn.size(); ++b) {
+    const double lmin = lamZ[lo[b]];
+    double Rb;
+    const int k = bc[b];
+    if (bk[b] == 0) {
+      Rb = s_count(nv, kappa) * std::pow(R, 2 * kappa);
+    } else {
+      const Poly& g = p.cl[k].g[gi[k]++];
+      const int dg = (g.degree(nv) + 1) / 2;
+      double gmax = 0.0;
+      for (int t = 0; t < g.nterms(); ++t) {
+        int deg = 0;
+        for (int v = 0; v < nv; ++v) deg += g.expo[(size_t)t * nv + v];
+        gmax += std::fabs(g.coef[t]) * std::pow(R, deg);
+      }
+      Rb = gmax * s_count(nv, kappa - dg) * std::pow(R, 2 * (kappa - dg));
+    }
+    lb += Rb * std::min(0.0, lmin);
+  }
+  out->max_ratio = max_ratio;
+  out->lower_bound = lb;
+  out->phat = phat;
+  out->xi = (phat - lb) / (1.0 + std::fabs(phat) + std::fabs(lb));
+  out->hmax = hmax;
+  out->gmin = gmin;
+  out->feasible = feasible;
+  out->rank_one = max_ratio <= rank_tol;
+  out->certified = out->rank_one && feasible && out->xi <= xi_tol;
+  if (zbar_out) std::copy(zbar.begin(), zbar.end(), zbar_out);
+  if (zhat_out) std::copy(zhat.begin(), zhat.end(), zhat_out);
+}
+
+}  // namespace
 }  // namespace strom
 
 using namespace strom;
@@ -151,73 +227,51 @@ extern "C" int strom_certify(strom_solver* s, int32_t i, const strom_problem* pr
       set_error("strom_certify: problem does not match the solver instance");
       return STROM_ERR_INVALID;
     }
-    const int nv = p.nv(), dx = p.dx, du = p.du;
-    std::vector<double> lam, top;
-    solver_eig_blocks(s, i, false, lam, top);
-    std::vector<double> zbar(p.nz(), 0.0);
-    double max_ratio = 0.0;
-    for (size_t b = 0; b < bn.size(); ++b) {
-      if (bk[b] != 0) continue;
-      const int n = bn[b];
-      const double l1 = lam[lo[b] + n - 1], l2 = lam[lo[b] + n - 2];
-      const double ratio = l1 > 0 ? l2 / l1 : INFINITY;
-      max_ratio = std::max(max_ratio, ratio);
-      const double v0 = top[lo[b]];
-      const int k = bc[b];
-      const int s0 = k * (dx + du);
-      for (int t = 0; t < dx + du; ++t) zbar[s0 + t] = top[lo[b] + 1 + t] / v0;
-      if (k == p.N - 1)
-        for (int t = dx + du; t < nv; ++t) zbar[s0 + t] = top[lo[b] + 1 + t] / v0;
-    }
-    std::vector<double> zhat = rollout(p, zbar);
-    double hmax = 0.0, gmin = INFINITY, phat = 0.0;
-    for (int k = 0; k < p.N; ++k) {
-      const double* zk = zhat.data() + k * (dx + du);
-      for (auto& h : p.cl[k].h) hmax = std::max(hmax, std::fabs(peval(h, nv, zk)));
-      for (auto& g : p.cl[k].g) gmin = std::min(gmin, peval(g, nv, zk));
-      phat += peval(p.cl[k].f, nv, zk);
-    }
-    const double feas_tol = 1e-9;
-    const bool feasible = hmax <= feas_tol && gmin >= -feas_tol;
-    // lower bound from lambda_min of Z = C - A^T y
-    solver_eig_blocks(s, i, true, lam, top);
-    const double R = std::max(1.0, p.R);
-    const int kappa = p.kappa;
-    double lb = by;
-    std::vector<int> gi(p.N, 0);
-    for (size_t b = 0; b < bn.size(); ++b) {
-      const double lmin = lam[lo[b]];
-      double Rb;
-      const int k = bc[b];
-      if (bk[b] == 0) {
-        Rb = s_count(nv, kappa) * std::pow(R, 2 * kappa);
-      } else {
-        const Poly& g = p.cl[k].g[gi[k]++];
-        const int dg = (g.degree(nv) + 1) / 2;
-        double gmax = 0.0;
-        for (int t = 0; t < g.nterms(); ++t) {
-          int deg = 0;
-          for (int v = 0; v < nv; ++v) deg += g.expo[(size_t)t * nv + v];
-          gmax += std::fabs(g.coef[t]) * std::pow(R, deg);
-        }
-        Rb = gmax * s_count(nv, kappa - dg) * std::pow(R, 2 * (kappa - dg));
-      }
-      lb += Rb * std::min(0.0, lmin);
-    }
-    out->max_ratio = max_ratio;
-    out->lower_bound = lb;
-    out->phat = phat;
-    out->xi = (phat - lb) / (1.0 + std::fabs(phat) + std::fabs(lb));
-    out->hmax = hmax;
-    out->gmin = gmin;
-    out->feasible = feasible;
-    out->rank_one = max_ratio <= rank_tol;
-    out->certified = out->rank_one && feasible && out->xi <= xi_tol;
-    if (zbar_out) std::copy(zbar.begin(), zbar.end(), zbar_out);
-    if (zhat_out) std::copy(zhat.begin(), zhat.end(), zhat_out);
+    std::vector<double> lamX, topX, lamZ, topZ;
+    solver_eig_blocks(s, i, false, lamX, topX);
+    solver_eig_blocks(s, i, true, lamZ, topZ);
+    certify_one(p, bn, bk, bc, lo.data(), lamX.data(), topX.data(), lamZ.data(), by, rank_tol, xi_tol, out, zbar_out,
+                zhat_out);
     return STROM_OK;
   } catch (const std::exception& e) {
     set_error(std::string("strom_certify: ") + e.what());
+    return STROM_ERR_CUDA;
+  }
+}
+
+extern "C" int strom_certify_batch(strom_solver* s, const strom_problem* const* problems, double rank_tol,
+                                   double xi_tol, strom_certificate* out) {
+  try {
+    if (!s || !problems || !out) {
+      set_error("strom_certify_batch: bad arguments");
+      return STROM_ERR_INVALID;
+    }
+    const int count = strom_solver_count(s);
+    for (int i = 0; i < count; ++i)
+      if (!problems[i]) {
+        set_error("strom_certify_batch: null problem");
+        return STROM_ERR_INVALID;
+      }
+    std::vector<double> lamX, topX, lamZ, topZ, stats;
+    std::vector<int64_t> lo;
+    solver_eig_all(s, false, lamX, topX, lo, stats);
+    solver_eig_all(s, true, lamZ, topZ, lo, stats);
+    for (int i = 0; i < count; ++i) {
+      const Problem& p = problems[i]->p;
+      std::vector<int32_t> bn, bc;
+      std::vector<int8_t> bk;
+      int64_t b0 = 0;
+      const int N = solver_inst_blocks(s, i, bn, bk, bc, &b0);
+      if (N != p.N) {
+        set_error("strom_certify_batch: problem does not match the solver instance");
+        return STROM_ERR_INVALID;
+      }
+      certify_one(p, bn, bk, bc, lo.data() + b0, lamX.data(), topX.data(), lamZ.data(), stats[8 * (size_t)i + 4],
+                  rank_tol, xi_tol, &out[i], nullptr, nullptr);
+    }
+    return STROM_OK;
+  } catch (const std::exception& e) {
+    set_error(std::string("strom_certify_batch: ") + e.what());
     return STROM_ERR_CUDA;
   }
 }

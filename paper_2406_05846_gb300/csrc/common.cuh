@@ -50,6 +50,7 @@ struct DevBuf {
   void upload(const T* h, size_t count, cudaStream_t st = 0) {
     alloc(count);
     if (count) STROM_CUDA(cudaMemcpyAsync(p, h, count * sizeof(T), cudaMemcpyHostToDevice, st));
+    count_h2d(count * sizeof(T));
   }
   void zero(cudaStream_t st = 0) {
     if (n) STROM_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), st));
@@ -57,6 +58,18 @@ struct DevBuf {
 };
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// host <-> device copies that are counted by strom_transfer_bytes()
+inline void copy_h2d(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (!bytes) return;
+  STROM_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
+  count_h2d(bytes);
+}
+inline void copy_d2h(void* dst, const void* src, size_t bytes, cudaStream_t st) {
+  if (!bytes) return;
+  STROM_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st));
+  count_d2h(bytes);
+}
 
 // ---------------------------------------------------------------------------
 // PSD projection launcher (psd.cu)

@@ -114,6 +114,8 @@ __global__ void __launch_bounds__(FT) chain_factor_kernel(YsolveDev d, double ra
         s_keep = keep;
         s_piv = keep ? sqrt(piv) : 1.0;
         d.keep[d.oth_rows[g0 + j]] = (uint8_t)keep;
+        d.keep_oth[g0 + j] = (uint8_t)keep;
+        d.inv_piv[g0 + j] = keep ? 1.0 / sqrt(piv) : 0.0;
         L[(int64_t)j * m + j] = s_piv;
       }
       __syncthreads();
@@ -129,6 +131,42 @@ __global__ void __launch_bounds__(FT) chain_factor_kernel(YsolveDev d, double ra
           double* coll = L + (int64_t)l * m;
           for (int i = l + lane; i < m; i += 32) coll[i] -= colj[i] * ljl;
         }
+      }
+      __syncthreads();
+    }
+    // inverses of the 32 x 32 diagonal blocks of L_g, with every dropped row j
+    // replaced by e_j in L and by 0 in the inverse (so w_j = y_j = 0 there);
+    // stored column-major per block: Dinv[t][j] at t * 32 + j.
+    {
+      const int nb = (m + 31) / 32;
+      double* Dg = d.dinv + d.dinv_off[g];
+      for (int b = warp; b < nb; b += FT / 32) {
+        const int jb = b * 32, je = min(jb + 32, m), bs = je - jb;
+        double* Db = Dg + (int64_t)b * 1024;
+        // lane k solves Ltilde x = e_k (forward substitution) for column k
+        const int k = lane;
+        double x[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) x[i] = 0.0;
+        if (k < bs && d.keep[d.oth_rows[g0 + jb + k]]) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            if (i < bs && i >= k) {
+              const int row = jb + i;
+              double acc = (i == k) ? 1.0 : 0.0;
+              if (d.keep[d.oth_rows[g0 + row]]) {
+#pragma unroll
+                for (int c = 0; c < 32; ++c)
+                  if (c >= k && c < i) acc -= L[(int64_t)(jb + c) * m + row] * x[c];
+                x[i] = acc / L[(int64_t)row * m + row];
+              } else {
+                x[i] = 0.0;
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 32; ++i) Db[(int64_t)k * 32 + i] = x[i];  // Dinv[i][k]
       }
       __syncthreads();
     }
@@ -171,20 +209,24 @@ __global__ void star_pre_kernel(YsolveDev d, const double* __restrict__ r, doubl
   rho[rep] = cc * acc / (1.0 + cc * d.star_d[c]) * d.inv_rep_s[rep];
 }
 
-// t_i = r_i + sum_p A_ip rho_p for every other row (written into y)
+// t_i = r_i + sum_p A_ip rho_p for every other row (written into yo, group order)
 __global__ void other_rhs_kernel(YsolveDev d, const double* __restrict__ r, const double* __restrict__ rho,
-                                 double* __restrict__ y) {
+                                 double* __restrict__ yo) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= d.noth) return;
   const int64_t row = d.oth_rows[q];
   if (d.inst_active && !d.inst_active[d.row_inst[row]]) return;
   double t = r[row];
   for (int64_t e = d.rowptr[row]; e < d.rowptr[row + 1]; ++e) t += d.val[e] * rho[d.col[e]];
-  y[row] = d.keep[row] ? t : 0.0;
+  yo[q] = d.keep_oth[q] ? t : 0.0;
 }
 
-// block forward / backward substitution along the chain; one CTA per instance
-__global__ void __launch_bounds__(FT) chain_solve_kernel(YsolveDev d, double* __restrict__ y) {
+// block forward / backward substitution along the chain; one CTA per instance.
+// The right-hand side arrives in yo (other rows, group order) and the
+// solution is written back to yo and scattered to y. Each 32 x 32 diagonal
+// block is applied through its precomputed inverse (a parallel product),
+// so no step of the substitution is a sequential chain of 32 divisions.
+__global__ void __launch_bounds__(FT) chain_solve_kernel(YsolveDev d, double* __restrict__ yo, double* __restrict__ y) {
   const int inst = blockIdx.x;
   if (d.inst_active && !d.inst_active[inst]) return;
   const int gbeg = d.inst_grp[inst], gend = d.inst_grp[inst + 1];
@@ -195,7 +237,7 @@ __global__ void __launch_bounds__(FT) chain_solve_kernel(YsolveDev d, double* __
     const int64_t g0 = d.grp_ptr[g];
     const int m = (int)(d.grp_ptr[g + 1] - g0);
     const double* L = d.fac + d.fac_off[g];
-    for (int i = threadIdx.x; i < m; i += FT) sh[i] = y[d.oth_rows[g0 + i]];
+    for (int i = threadIdx.x; i < m; i += FT) sh[i] = yo[g0 + i];
     __syncthreads();
     if (g + 1 < gend) {
       const int cn = d.coup_n[g + 1];
@@ -204,36 +246,33 @@ __global__ void __launch_bounds__(FT) chain_solve_kernel(YsolveDev d, double* __
       const double* E = d.coup + d.coup_off[g + 1];
       for (int a = warp; a < cn; a += FT / 32) {
         double s = 0.0;
-        for (int rr = lane; rr < nm; rr += 32) s += E[(int64_t)a * nm + rr] * y[d.oth_rows[ng0 + rr]];
+        for (int rr = lane; rr < nm; rr += 32) s += E[(int64_t)a * nm + rr] * yo[ng0 + rr];
         s = warp_sum(s);
         if (lane == 0) sh[m - cn + a] -= s;
       }
       __syncthreads();
     }
+    const double* Dg = d.dinv + d.dinv_off[g];
     for (int jb = 0; jb < m; jb += 32) {
-      const int je = min(jb + 32, m);
-      if (warp == 0) {
-        const int j = jb + lane;
-        double tj = (j < je) ? sh[j] : 0.0;
-        const uint8_t kj = (j < je) ? d.keep[d.oth_rows[g0 + j]] : 0;
-        for (int jj = jb; jj < je; ++jj) {
-          double w = 0.0;
-          if (lane == jj - jb) w = kj ? tj / L[(int64_t)jj * m + jj] : 0.0;
-          w = __shfl_sync(0xffffffffu, w, jj - jb);
-          if (j > jj && j < je) tj -= L[(int64_t)jj * m + j] * w;
-          if (lane == jj - jb) tj = w;
-        }
-        if (j < je) sh[j] = tj;
+      const int je = min(jb + 32, m), bs = je - jb;
+      const double* Db = Dg + (int64_t)(jb / 32) * 1024;
+      // w_b = Dinv_b t_b  (threads 0..31, column-major Dinv: coalesced)
+      double w = 0.0;
+      if (threadIdx.x < 32) {
+        const int j = threadIdx.x;
+        for (int t = 0; t < bs; ++t) w += Db[t * 32 + j] * sh[jb + t];
       }
       __syncthreads();
+      if (threadIdx.x < bs) sh[jb + threadIdx.x] = w;
+      __syncthreads();
       for (int i = je + threadIdx.x; i < m; i += FT) {
-        double s = 0.0;
-        for (int jj = jb; jj < je; ++jj) s += L[(int64_t)jj * m + i] * sh[jj];
-        sh[i] -= s;
+        double acc = 0.0;
+        for (int jj = jb; jj < je; ++jj) acc += L[(int64_t)jj * m + i] * sh[jj];
+        sh[i] -= acc;
       }
       __syncthreads();
     }
-    for (int i = threadIdx.x; i < m; i += FT) y[d.oth_rows[g0 + i]] = sh[i];
+    for (int i = threadIdx.x; i < m; i += FT) yo[g0 + i] = sh[i];
     __syncthreads();
   }
   // backward: groups gbeg .. gend-1,  y_g = L_g^{-T} (w_g - E_g y_{g-1}[cons])
@@ -241,13 +280,13 @@ __global__ void __launch_bounds__(FT) chain_solve_kernel(YsolveDev d, double* __
     const int64_t g0 = d.grp_ptr[g];
     const int m = (int)(d.grp_ptr[g + 1] - g0);
     const double* L = d.fac + d.fac_off[g];
+    const double* Dg = d.dinv + d.dinv_off[g];
     const int cprev = d.coup_n[g];
     const double* E = d.coup + d.coup_off[g];
-    const int64_t pg0 = (g > gbeg) ? d.grp_ptr[g - 1] : 0;
-    const int pm = (g > gbeg) ? (int)(d.grp_ptr[g] - pg0) : 0;
+    const int64_t pcons0 = (g > gbeg) ? d.grp_ptr[g] - cprev : 0;  // consensus rows ending group g-1
     for (int i = threadIdx.x; i < m; i += FT) {
-      double w = y[d.oth_rows[g0 + i]];
-      for (int c = 0; c < cprev; ++c) w -= E[(int64_t)c * m + i] * y[d.oth_rows[pg0 + pm - cprev + c]];
+      double w = yo[g0 + i];
+      for (int c = 0; c < cprev; ++c) w -= E[(int64_t)c * m + i] * yo[pcons0 + c];
       sh[i] = w;
     }
     __syncthreads();
@@ -263,22 +302,21 @@ __global__ void __launch_bounds__(FT) chain_solve_kernel(YsolveDev d, double* __
         if (lane == 0) sh[j] -= s;
       }
       __syncthreads();
-      if (warp == 0) {
-        const int j = jb + lane;
-        double wj = (j < je) ? sh[j] : 0.0;
-        const uint8_t kj = (j < je) ? d.keep[d.oth_rows[g0 + j]] : 0;
-        for (int jj = je - 1; jj >= jb; --jj) {
-          double v = 0.0;
-          if (lane == jj - jb) v = kj ? wj / L[(int64_t)jj * m + jj] : 0.0;
-          v = __shfl_sync(0xffffffffu, v, jj - jb);
-          if (j < jj) wj -= L[(int64_t)j * m + jj] * v;
-          if (lane == jj - jb) wj = v;
-        }
-        if (j < je) sh[j] = wj;
+      // y_b = Dinv_b^T w_b
+      const double* Db = Dg + (int64_t)b * 1024;
+      double v = 0.0;
+      if (threadIdx.x < 32) {
+        const int j = threadIdx.x;
+        for (int t = 0; t < je - jb; ++t) v += Db[(int64_t)j * 32 + t] * sh[jb + t];
       }
       __syncthreads();
+      if (threadIdx.x < je - jb) sh[jb + threadIdx.x] = v;
+      __syncthreads();
     }
-    for (int i = threadIdx.x; i < m; i += FT) y[d.oth_rows[g0 + i]] = sh[i];
+    for (int i = threadIdx.x; i < m; i += FT) {
+      yo[g0 + i] = sh[i];
+      y[d.oth_rows[g0 + i]] = sh[i];
+    }
     __syncthreads();
   }
 }
@@ -311,8 +349,10 @@ __global__ void star_post_kernel(YsolveDev d, const double* __restrict__ r, doub
 void ysolve_factor(const YsolveDev& d, int ngroups, int ninst, double rank_tol, cudaStream_t st) {
   assemble_kernel<<<ngroups, FT, 0, st>>>(d);
   STROM_CUDA(cudaGetLastError());
+  count_launches(1);
   chain_factor_kernel<<<ninst, FT, 0, st>>>(d, rank_tol);
   STROM_CUDA(cudaGetLastError());
+  count_launches(1);
 }
 
 void ysolve_apply(const YsolveDev& d, int ninst, int max_group, const double* r, double* y, double* rho,
@@ -320,14 +360,18 @@ void ysolve_apply(const YsolveDev& d, int ninst, int max_group, const double* r,
   if (d.nclass > 0) {
     star_pre_kernel<<<ceil_div(d.nclass, 256), 256, 0, st>>>(d, r, rho);
     STROM_CUDA(cudaGetLastError());
+    count_launches(1);
   }
-  other_rhs_kernel<<<ceil_div(d.noth, 256), 256, 0, st>>>(d, r, rho, y);
+  other_rhs_kernel<<<ceil_div(d.noth, 256), 256, 0, st>>>(d, r, rho, d.yo);
   STROM_CUDA(cudaGetLastError());
-  chain_solve_kernel<<<ninst, FT, sizeof(double) * max_group, st>>>(d, y);
+  count_launches(1);
+  chain_solve_kernel<<<ninst, FT, sizeof(double) * max_group, st>>>(d, d.yo, y);
   STROM_CUDA(cudaGetLastError());
+  count_launches(1);
   if (d.nclass > 0) {
     star_post_kernel<<<ceil_div(d.nclass, 256), 256, 0, st>>>(d, r, y);
     STROM_CUDA(cudaGetLastError());
+    count_launches(1);
   }
 }
 

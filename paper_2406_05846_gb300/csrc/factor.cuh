@@ -40,6 +40,11 @@ struct YsolveDev {
   const int64_t* coup_off;
   double* diag0;             // [noth]
   uint8_t* keep;             // [m_total]
+  uint8_t* keep_oth;         // [noth] keep flag of each other row, group order
+  double* yo;                // [noth] work vector of the chain solve, group order
+  double* inv_piv;           // [noth] 1 / pivot of each kept other row, 0 if dropped
+  double* dinv;              // inverses of the 32 x 32 diagonal blocks of every L_g
+  const int64_t* dinv_off;   // [ngroups]
   const uint8_t* inst_active;  // nullable
 };
 

@@ -9,6 +9,9 @@
 namespace strom {
 
 void set_error(const std::string& msg);
+void count_launches(int64_t n);   // bookkeeping behind strom_launch_count()
+void count_h2d(uint64_t bytes);
+void count_d2h(uint64_t bytes);
 
 struct Poly {
   std::vector<double> coef;

@@ -238,6 +238,7 @@ void launch_class(const PsdArgs& a, int start, int count, double tol, int sweeps
   using SM = JacobiSmem<T, NP, NT, VSMEM>;
   jacobi_psd_kernel<T, NP, NT, VSMEM><<<count, NT, SM::total, st>>>(a, start, tol, sweeps);
   STROM_CUDA(cudaGetLastError());
+  count_launches(1);
 }
 
 }  // namespace

@@ -47,9 +47,10 @@ struct strom_solver {
   DevBuf<int32_t> inst_svec_chunk, inst_row_chunk, iters, n_active;
   DevBuf<double> val, atval, b, C, omega, inv_rep_s, star_c, star_d, star_inv_s2, fac, coup, diag0;
   DevBuf<double> X, S, Xb, y, yh, r, rho, norm_b, norm_C, sigma, stats, part_svec, part_rows, blk_inv_sigma;
-  DevBuf<double> vscratch, tmp_svec, lam, topvec;
+  DevBuf<double> vscratch, tmp_svec, lam, topvec, yo, inv_piv, dinv;
+  DevBuf<int64_t> dinv_off;
   DevBuf<int8_t> row_kind;
-  DevBuf<uint8_t> keep, inst_active, inst_flag, inst_prec, blk_act32, blk_act64;
+  DevBuf<uint8_t> keep, keep_oth, inst_active, inst_flag, inst_prec, blk_act32, blk_act64;
   DevBuf<Chunk> svec_chunks, row_chunks;
   PsdClasses cls;
   YsolveDev yd{};
@@ -58,6 +59,7 @@ struct strom_solver {
   cudaStream_t stream = nullptr;
   cudaGraphExec_t graph = nullptr;
   cudaGraph_t graph_def = nullptr;
+  int64_t graph_kernels = 0;  // kernel nodes of one captured iteration
   ~strom_solver() {
     if (graph) cudaGraphExecDestroy(graph);
     if (graph_def) cudaGraphDestroy(graph_def);
@@ -135,6 +137,7 @@ void build_graph(strom_solver* s) {
   if (s->graph) return;
   psd_configure();
   STROM_CUDA(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+  const uint64_t before = strom_launch_count();
   try {
     enqueue_iteration(s, s->stream);
   } catch (...) {
@@ -144,6 +147,8 @@ void build_graph(strom_solver* s) {
     throw;
   }
   STROM_CUDA(cudaStreamEndCapture(s->stream, &s->graph_def));
+  s->graph_kernels = (int64_t)(strom_launch_count() - before);
+  count_launches(-s->graph_kernels);  // captured, not launched
   STROM_CUDA(cudaGraphInstantiate(&s->graph, s->graph_def, 0));
 }
 
@@ -158,10 +163,30 @@ void reset_state(strom_solver* s) {
   std::vector<double> sg(s->ninst, s->opt.sigma0);
   std::vector<uint8_t> one(s->ninst, 1);
   std::vector<uint8_t> prec(s->ninst, (uint8_t)(s->opt.precision == STROM_PREC_FP64 ? STROM_PREC_FP64 : STROM_PREC_FP32));
-  STROM_CUDA(cudaMemcpyAsync(s->sigma.p, sg.data(), sizeof(double) * s->ninst, cudaMemcpyHostToDevice, s->stream));
-  STROM_CUDA(cudaMemcpyAsync(s->inst_active.p, one.data(), s->ninst, cudaMemcpyHostToDevice, s->stream));
-  STROM_CUDA(cudaMemcpyAsync(s->inst_prec.p, prec.data(), s->ninst, cudaMemcpyHostToDevice, s->stream));
+  copy_h2d(s->sigma.p, sg.data(), sizeof(double) * s->ninst, s->stream);
+  copy_h2d(s->inst_active.p, one.data(), s->ninst, s->stream);
+  copy_h2d(s->inst_prec.p, prec.data(), s->ninst, s->stream);
   STROM_CUDA(cudaStreamSynchronize(s->stream));
+}
+
+// row reduction + factorisation of A A^T from the device data, ||b_K|| per
+// instance, and a fresh state
+void refactor(strom_solver* s) {
+  cudaStream_t st = s->stream;
+  ysolve_factor(s->yd, s->ngroups, s->ninst, s->opt.rank_tol, st);
+  std::vector<uint8_t> keep(s->m);
+  copy_d2h(keep.data(), s->keep.p, s->m, st);
+  STROM_CUDA(cudaStreamSynchronize(st));
+  std::vector<double> nb(s->ninst, 0.0);
+  s->m_kept.assign(s->ninst, 0);
+  for (int i = 0; i < s->ninst; ++i) {
+    const auto& b = s->meta[i].b;
+    for (int64_t r = 0; r < (int64_t)b.size(); ++r)
+      if (keep[s->row_off[i] + r]) { nb[i] += b[r] * b[r]; s->m_kept[i]++; }
+    nb[i] = std::sqrt(nb[i]);
+  }
+  copy_h2d(s->norm_b.p, nb.data(), sizeof(double) * s->ninst, st);
+  reset_state(s);
 }
 
 void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
@@ -177,14 +202,14 @@ void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
   s->m = s->row_off[count];
   if (s->nsvec > INT32_MAX || s->m > INT32_MAX) throw StatusError(STROM_ERR_INVALID, "batch too large for int32 indices");
   // ---- concatenated host arrays
-  std::vector<int64_t> rowptr(1, 0), star_rep, star_row, oth_rows, grp_ptr(1, 0), fac_off(1, 0), coup_off(1, 0), blk_off,
+  std::vector<int64_t> dinv_off, rowptr(1, 0), star_rep, star_row, oth_rows, grp_ptr(1, 0), fac_off(1, 0), coup_off(1, 0), blk_off,
       lam_off;
   std::vector<int32_t> col, row_inst, star_ptr, star_inst, inst_grp(1, 0), coup_n, blk_n, blk_inst;
   std::vector<double> val, b, C, omega, inv_rep_s, star_c, star_d, star_inv_s2;
   std::vector<int8_t> row_kind;
   std::vector<double> normC(count);
   s->inst_blk_off.assign(count + 1, 0);
-  int64_t lam_acc = 0;
+  int64_t lam_acc = 0, dinv_acc = 0;
   for (int i = 0; i < count; ++i) {
     const Sdp& q = *sdps[i]->s;
     const int64_t so = s->svec_off[i], ro = s->row_off[i];
@@ -229,6 +254,8 @@ void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
       const int cprev = (k > 0) ? q.grp_cons[k - 1] : 0;
       coup_n.push_back(cprev);
       fac_off.push_back(fac_off.back() + mk * mk);
+      dinv_off.push_back(dinv_acc);
+      dinv_acc += ((mk + 31) / 32) * 1024;
       coup_off.push_back(coup_off.back() + mk * cprev);
       s->max_group = std::max<int>(s->max_group, (int)mk);
     }
@@ -310,6 +337,12 @@ void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
   s->coup.alloc(std::max<int64_t>(1, coup_off.back()));
   s->diag0.alloc(std::max<size_t>(1, oth_rows.size()));
   s->keep.alloc(s->m);
+  s->keep_oth.alloc(std::max<size_t>(1, oth_rows.size()));
+  s->yo.alloc(std::max<size_t>(1, oth_rows.size()));
+  s->yo.zero(st);
+  s->inv_piv.alloc(std::max<size_t>(1, oth_rows.size()));
+  s->dinv.alloc(std::max<int64_t>(1, dinv_acc));
+  s->dinv_off.upload(dinv_off.data(), dinv_off.size(), st);
   STROM_CUDA(cudaMemsetAsync(s->keep.p, 1, s->m, st));
   for (auto* v : {&s->X, &s->S, &s->Xb, &s->rho, &s->tmp_svec}) v->alloc(s->nsvec);
   s->rho.zero(st);
@@ -342,7 +375,8 @@ void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
   yd.noth = (int64_t)oth_rows.size(); yd.oth_rows = s->oth_rows.p; yd.grp_ptr = s->grp_ptr.p;
   yd.inst_grp = s->inst_grp.p; yd.coup_n = s->coup_n.p;
   yd.fac = s->fac.p; yd.fac_off = s->fac_off.p; yd.coup = s->coup.p; yd.coup_off = s->coup_off.p;
-  yd.diag0 = s->diag0.p; yd.keep = s->keep.p; yd.inst_active = nullptr;
+  yd.diag0 = s->diag0.p; yd.keep = s->keep.p; yd.keep_oth = s->keep_oth.p; yd.yo = s->yo.p; yd.inv_piv = s->inv_piv.p; yd.dinv = s->dinv.p; yd.dinv_off = s->dinv_off.p;
+  yd.inst_active = nullptr;
   AdmmDev& ad = s->ad;
   ad.ninst = count; ad.nblk = s->nblk;
   ad.n_svec_chunks = (int)sch.size(); ad.n_row_chunks = (int)rch.size();
@@ -362,19 +396,7 @@ void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
   p.sigma_min = s->opt.sigma_min; p.sigma_max = s->opt.sigma_max;
   p.precision = s->opt.precision; p.polish_eta = s->opt.polish_eta;
   // ---- row reduction + factorisation (once)
-  ysolve_factor(yd, s->ngroups, count, s->opt.rank_tol, st);
-  STROM_CUDA(cudaStreamSynchronize(st));
-  std::vector<uint8_t> keep(s->m);
-  STROM_CUDA(cudaMemcpy(keep.data(), s->keep.p, s->m, cudaMemcpyDeviceToHost));
-  std::vector<double> nb(count, 0.0);
-  s->m_kept.assign(count, 0);
-  for (int i = 0; i < count; ++i) {
-    for (int64_t r = s->row_off[i]; r < s->row_off[i + 1]; ++r)
-      if (keep[r]) { nb[i] += b[r] * b[r]; s->m_kept[i]++; }
-    nb[i] = std::sqrt(nb[i]);
-  }
-  s->norm_b.upload(nb.data(), count, st);
-  reset_state(s);
+  refactor(s);
 }
 
 }  // namespace
@@ -451,8 +473,9 @@ extern "C" int strom_solver_step(strom_solver* s, int32_t iters, void* stream, i
     while (done < iters) {
       const int n = std::min(iters - done, s->opt.check_every);
       for (int k = 0; k < n; ++k) STROM_CUDA(cudaGraphLaunch(s->graph, s->stream));
+      count_launches(s->graph_kernels * n);
       done += n;
-      STROM_CUDA(cudaMemcpyAsync(&act, s->n_active.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+      copy_d2h(&act, s->n_active.p, sizeof(int32_t), s->stream);
       STROM_CUDA(cudaStreamSynchronize(s->stream));
       if (act == 0) break;
     }
@@ -468,13 +491,25 @@ extern "C" int strom_solver_step(strom_solver* s, int32_t iters, void* stream, i
   });
 }
 
+extern "C" int strom_solver_factor(strom_solver* s, void* stream) {
+  return guard([&] {
+    if (!s) throw StatusError(STROM_ERR_INVALID, "strom_solver_factor: null solver");
+    if (stream) STROM_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    refactor(s);
+    return STROM_OK;
+  });
+}
+
 extern "C" int strom_solve(strom_solver* s, void* stream) {
   int32_t act = 1;
   int st = strom_solver_step(s, s ? s->opt.maxiter : 0, stream, &act);
   if (st != STROM_OK) return st;
   std::vector<uint8_t> flag(s->ninst);
-  if (cudaMemcpy(flag.data(), s->inst_flag.p, s->ninst, cudaMemcpyDeviceToHost) != cudaSuccess) {
-    set_error("strom_solve: copy of the instance flags failed");
+  try {
+    copy_d2h(flag.data(), s->inst_flag.p, s->ninst, s->stream);
+    STROM_CUDA(cudaStreamSynchronize(s->stream));
+  } catch (const std::exception& e) {
+    set_error(std::string("strom_solve: ") + e.what());
     return STROM_ERR_CUDA;
   }
   for (uint8_t f : flag)
@@ -494,20 +529,20 @@ extern "C" int strom_solver_reset(strom_solver* s, int32_t i, const double* X0, 
     const int64_t so = s->svec_off[i], n = s->svec_off[i + 1] - so;
     const int64_t ro = s->row_off[i], m = s->row_off[i + 1] - ro;
     cudaStream_t st = s->stream;
-    if (X0) STROM_CUDA(cudaMemcpyAsync(s->X.p + so, X0, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (X0) copy_h2d(s->X.p + so, X0, n * sizeof(double), st);
     else STROM_CUDA(cudaMemsetAsync(s->X.p + so, 0, n * sizeof(double), st));
-    if (S0) STROM_CUDA(cudaMemcpyAsync(s->S.p + so, S0, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (S0) copy_h2d(s->S.p + so, S0, n * sizeof(double), st);
     else STROM_CUDA(cudaMemsetAsync(s->S.p + so, 0, n * sizeof(double), st));
     STROM_CUDA(cudaMemsetAsync(s->y.p + ro, 0, m * sizeof(double), st));
     const double sg = sigma > 0 ? sigma : s->opt.sigma0;
     const uint8_t one = 1, zero = 0;
     const uint8_t prec = (uint8_t)(s->opt.precision == STROM_PREC_FP64 ? STROM_PREC_FP64 : STROM_PREC_FP32);
     const int32_t zi = 0;
-    STROM_CUDA(cudaMemcpyAsync(s->sigma.p + i, &sg, sizeof(double), cudaMemcpyHostToDevice, st));
-    STROM_CUDA(cudaMemcpyAsync(s->inst_active.p + i, &one, 1, cudaMemcpyHostToDevice, st));
-    STROM_CUDA(cudaMemcpyAsync(s->inst_flag.p + i, &zero, 1, cudaMemcpyHostToDevice, st));
-    STROM_CUDA(cudaMemcpyAsync(s->inst_prec.p + i, &prec, 1, cudaMemcpyHostToDevice, st));
-    STROM_CUDA(cudaMemcpyAsync(s->iters.p + i, &zi, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    copy_h2d(s->sigma.p + i, &sg, sizeof(double), st);
+    copy_h2d(s->inst_active.p + i, &one, 1, st);
+    copy_h2d(s->inst_flag.p + i, &zero, 1, st);
+    copy_h2d(s->inst_prec.p + i, &prec, 1, st);
+    copy_h2d(s->iters.p + i, &zi, sizeof(int32_t), st);
     STROM_CUDA(cudaStreamSynchronize(st));
     return STROM_OK;
   });
@@ -520,10 +555,10 @@ extern "C" int strom_get_result(const strom_solver* s, int32_t i, strom_result* 
     int32_t it;
     uint8_t flag;
     double sg;
-    STROM_CUDA(cudaMemcpy(st, s->stats.p + 8 * (int64_t)i, sizeof(st), cudaMemcpyDeviceToHost));
-    STROM_CUDA(cudaMemcpy(&it, s->iters.p + i, sizeof(int32_t), cudaMemcpyDeviceToHost));
-    STROM_CUDA(cudaMemcpy(&flag, s->inst_flag.p + i, 1, cudaMemcpyDeviceToHost));
-    STROM_CUDA(cudaMemcpy(&sg, s->sigma.p + i, sizeof(double), cudaMemcpyDeviceToHost));
+    copy_d2h(st, s->stats.p + 8 * (int64_t)i, sizeof(st), s->stream); STROM_CUDA(cudaStreamSynchronize(s->stream));
+    copy_d2h(&it, s->iters.p + i, sizeof(int32_t), s->stream); STROM_CUDA(cudaStreamSynchronize(s->stream));
+    copy_d2h(&flag, s->inst_flag.p + i, 1, s->stream); STROM_CUDA(cudaStreamSynchronize(s->stream));
+    copy_d2h(&sg, s->sigma.p + i, sizeof(double), s->stream); STROM_CUDA(cudaStreamSynchronize(s->stream));
     r->status = flag == 1 ? STROM_OK : flag == 2 ? STROM_ERR_NUMERICAL : STROM_MAXITER;
     r->iterations = it;
     r->eta_p = st[0]; r->eta_d = st[1]; r->eta_g = st[2]; r->pobj = st[3]; r->dobj = st[4];
@@ -538,9 +573,9 @@ extern "C" int strom_get_state(const strom_solver* s, int32_t i, double* X, doub
     if (!s || i < 0 || i >= s->ninst) throw StatusError(STROM_ERR_INVALID, "strom_get_state: bad instance");
     const int64_t so = s->svec_off[i], n = s->svec_off[i + 1] - so;
     const int64_t ro = s->row_off[i], m = s->row_off[i + 1] - ro;
-    if (X) STROM_CUDA(cudaMemcpy(X, s->X.p + so, n * sizeof(double), cudaMemcpyDeviceToHost));
-    if (S) STROM_CUDA(cudaMemcpy(S, s->S.p + so, n * sizeof(double), cudaMemcpyDeviceToHost));
-    if (y) STROM_CUDA(cudaMemcpy(y, s->y.p + ro, m * sizeof(double), cudaMemcpyDeviceToHost));
+    if (X) copy_d2h(X, s->X.p + so, n * sizeof(double), s->stream); STROM_CUDA(cudaStreamSynchronize(s->stream));
+    if (S) copy_d2h(S, s->S.p + so, n * sizeof(double), s->stream); STROM_CUDA(cudaStreamSynchronize(s->stream));
+    if (y) copy_d2h(y, s->y.p + ro, m * sizeof(double), s->stream); STROM_CUDA(cudaStreamSynchronize(s->stream));
     return STROM_OK;
   });
 }
@@ -549,7 +584,7 @@ extern "C" int strom_get_kept_rows(const strom_solver* s, int32_t i, uint8_t* ke
   return guard([&] {
     if (!s || !keep || i < 0 || i >= s->ninst) throw StatusError(STROM_ERR_INVALID, "strom_get_kept_rows: bad arguments");
     const int64_t ro = s->row_off[i], m = s->row_off[i + 1] - ro;
-    STROM_CUDA(cudaMemcpy(keep, s->keep.p + ro, m, cudaMemcpyDeviceToHost));
+    copy_d2h(keep, s->keep.p + ro, m, s->stream); STROM_CUDA(cudaStreamSynchronize(s->stream));
     return STROM_OK;
   });
 }
@@ -564,8 +599,8 @@ extern "C" int strom_get_moment(const strom_solver* s, int32_t i, int32_t k, dou
     if (blk < 0) throw StatusError(STROM_ERR_INVALID, "strom_get_moment: no such clique");
     const int n = mt.block_n[blk];
     std::vector<double> v((size_t)n * (n + 1) / 2);
-    STROM_CUDA(cudaMemcpy(v.data(), s->X.p + s->svec_off[i] + mt.block_off[blk], v.size() * sizeof(double),
-                          cudaMemcpyDeviceToHost));
+    copy_d2h(v.data(), s->X.p + s->svec_off[i] + mt.block_off[blk], v.size() * sizeof(double), s->stream);
+    STROM_CUDA(cudaStreamSynchronize(s->stream));
     for (int j = 0; j < n; ++j)
       for (int q = 0; q <= j; ++q) {
         const double x = v[(size_t)j * (j + 1) / 2 + q] * (q == j ? 1.0 : 0.70710678118654752440);
@@ -608,6 +643,10 @@ struct CertDevice {
   const strom_solver* s;
 };
 void solver_eig_blocks(strom_solver* s, int inst, bool use_Z, std::vector<double>& lam, std::vector<double>& topvec);
+void solver_eig_all(strom_solver* s, bool use_Z, std::vector<double>& lam, std::vector<double>& topvec,
+                    std::vector<int64_t>& lam_off, std::vector<double>& stats);
+int solver_inst_blocks(const strom_solver* s, int inst, std::vector<int32_t>& n, std::vector<int8_t>& kind,
+                       std::vector<int32_t>& clique, int64_t* first_blk);
 }  // namespace strom
 
 namespace {
@@ -630,13 +669,14 @@ void strom::solver_eig_blocks(strom_solver* s, int inst, bool use_Z, std::vector
     z_kernel<<<ceil_div(se - so, 256), 256, 0, s->stream>>>(s->atptr.p, s->atrow.p, s->atval.p, s->y.p, s->C.p, so, se,
                                                           s->tmp_svec.p);
     STROM_CUDA(cudaGetLastError());
+    count_launches(1);
     in = s->tmp_svec.p;
   }
   // a block list with only this instance's blocks
   const int b0 = (int)s->inst_blk_off[inst], b1 = (int)s->inst_blk_off[inst + 1];
   std::vector<int32_t> bn(b1 - b0), ids;
   std::vector<int32_t> nall(s->nblk);
-  STROM_CUDA(cudaMemcpy(nall.data(), s->blk_n.p, sizeof(int32_t) * s->nblk, cudaMemcpyDeviceToHost));
+  copy_d2h(nall.data(), s->blk_n.p, sizeof(int32_t) * s->nblk, s->stream); STROM_CUDA(cudaStreamSynchronize(s->stream));
   PsdClasses cls;
   std::vector<std::vector<int32_t>> per(4);
   for (int b = b0; b < b1; ++b) {
@@ -666,8 +706,52 @@ void strom::solver_eig_blocks(strom_solver* s, int inst, bool use_Z, std::vector
   STROM_CUDA(cudaStreamSynchronize(s->stream));
   lam.assign(s->lam.n, 0.0);
   topvec.assign(s->topvec.n, 0.0);
-  STROM_CUDA(cudaMemcpy(lam.data(), s->lam.p, sizeof(double) * lam.size(), cudaMemcpyDeviceToHost));
-  STROM_CUDA(cudaMemcpy(topvec.data(), s->topvec.p, sizeof(double) * topvec.size(), cudaMemcpyDeviceToHost));
+  copy_d2h(lam.data(), s->lam.p, sizeof(double) * lam.size(), s->stream); STROM_CUDA(cudaStreamSynchronize(s->stream));
+  copy_d2h(topvec.data(), s->topvec.p, sizeof(double) * topvec.size(), s->stream); STROM_CUDA(cudaStreamSynchronize(s->stream));
+}
+
+// eigenvalues (ascending) and top eigenvectors of every block of the batch,
+// for X (use_Z = false) or Z = C - A^T y (use_Z = true); FP64 Jacobi
+void strom::solver_eig_all(strom_solver* s, bool use_Z, std::vector<double>& lam, std::vector<double>& topvec,
+                           std::vector<int64_t>& lam_off, std::vector<double>& stats) {
+  const double* in = s->X.p;
+  if (use_Z) {
+    z_kernel<<<ceil_div(s->nsvec, 256), 256, 0, s->stream>>>(s->atptr.p, s->atrow.p, s->atval.p, s->y.p, s->C.p, 0,
+                                                            s->nsvec, s->tmp_svec.p);
+    STROM_CUDA(cudaGetLastError());
+    count_launches(1);
+    in = s->tmp_svec.p;
+  }
+  PsdArgs a{};
+  a.Xb = in;
+  a.out = nullptr;
+  a.blk_off = s->blk_off.p;
+  a.blk_n = s->blk_n.p;
+  a.blk_list = s->blk_list.p;
+  a.lam = s->lam.p;
+  a.lam_off = s->lam_off.p;
+  a.topvec = s->topvec.p;
+  a.vscratch = s->vscratch.p;
+  psd_launch(a, s->cls, STROM_PREC_FP64, s->stream);
+  lam.assign(s->lam.n, 0.0);
+  topvec.assign(s->topvec.n, 0.0);
+  lam_off.assign(s->nblk, 0);
+  stats.assign(8 * (size_t)s->ninst, 0.0);
+  copy_d2h(lam.data(), s->lam.p, sizeof(double) * lam.size(), s->stream);
+  copy_d2h(topvec.data(), s->topvec.p, sizeof(double) * topvec.size(), s->stream);
+  copy_d2h(lam_off.data(), s->lam_off.p, sizeof(int64_t) * s->nblk, s->stream);
+  copy_d2h(stats.data(), s->stats.p, sizeof(double) * stats.size(), s->stream);
+  STROM_CUDA(cudaStreamSynchronize(s->stream));
+}
+
+int strom::solver_inst_blocks(const strom_solver* s, int inst, std::vector<int32_t>& n, std::vector<int8_t>& kind,
+                              std::vector<int32_t>& clique, int64_t* first_blk) {
+  const InstMeta& mt = s->meta[inst];
+  n = mt.block_n;
+  kind = mt.block_kind;
+  clique = mt.block_clique;
+  *first_blk = s->inst_blk_off[inst];
+  return mt.N;
 }
 
 namespace strom {
@@ -679,16 +763,16 @@ int solver_blocks_of(const strom_solver* s, int inst, std::vector<int32_t>& n, s
   clique = mt.block_clique;
   lam_off.clear();
   std::vector<int64_t> all(s->nblk);
-  STROM_CUDA(cudaMemcpy(all.data(), s->lam_off.p, sizeof(int64_t) * s->nblk, cudaMemcpyDeviceToHost));
+  copy_d2h(all.data(), s->lam_off.p, sizeof(int64_t) * s->nblk, s->stream); STROM_CUDA(cudaStreamSynchronize(s->stream));
   for (int64_t b = s->inst_blk_off[inst]; b < s->inst_blk_off[inst + 1]; ++b) lam_off.push_back(all[b]);
   double st[8];
-  STROM_CUDA(cudaMemcpy(st, s->stats.p + 8 * (int64_t)inst, sizeof(st), cudaMemcpyDeviceToHost));
+  copy_d2h(st, s->stats.p + 8 * (int64_t)inst, sizeof(st), s->stream); STROM_CUDA(cudaStreamSynchronize(s->stream));
   // <b, y> over kept rows of this instance, recomputed from the current y
   const int64_t ro = s->row_off[inst], m = s->row_off[inst + 1] - ro;
   std::vector<double> y(m);
   std::vector<uint8_t> keep(m);
-  STROM_CUDA(cudaMemcpy(y.data(), s->y.p + ro, m * sizeof(double), cudaMemcpyDeviceToHost));
-  STROM_CUDA(cudaMemcpy(keep.data(), s->keep.p + ro, m, cudaMemcpyDeviceToHost));
+  copy_d2h(y.data(), s->y.p + ro, m * sizeof(double), s->stream); STROM_CUDA(cudaStreamSynchronize(s->stream));
+  copy_d2h(keep.data(), s->keep.p + ro, m, s->stream); STROM_CUDA(cudaStreamSynchronize(s->stream));
   double acc = 0.0;
   for (int64_t r = 0; r < m; ++r)
     if (keep[r]) acc += mt.b[r] * y[r];
