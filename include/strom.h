@@ -27,6 +27,7 @@ extern "C" {
 enum {
   STROM_OK = 0,
   STROM_MAXITER = 1,          /* results valid, tolerance not reached */
+  STROM_PENDING = 2,          /* a served request has not finished yet */
   STROM_ERR_INVALID = -1,     /* bad argument or malformed problem */
   STROM_ERR_OOM = -2,         /* device or host allocation failed */
   STROM_ERR_NOT_PD = -3,      /* A A^T not positive definite after row reduction */
@@ -210,6 +211,31 @@ uint64_t strom_launch_count(void);
 /* Bytes libstrom has copied host->device and device->host in this process. */
 void strom_transfer_bytes(uint64_t* h2d, uint64_t* d2h);
 
+/* ------------------------------------------------------------------------
+ * Serving by continuous batching. A batch owns `slots` solver slots for
+ * SDPs with the structure of `tmpl` (same horizon, blocks, rows and sparsity
+ * pattern; values of A, b and C may differ, as they do between initial
+ * states). Submitted requests wait in a FIFO queue until a slot is free.
+ * Each step admits queued requests into free slots (upload, row reduction
+ * and factorisation of just those slots), runs `iters` iterations of
+ * Algorithm 1 on every occupied slot, and retires the requests that met tol
+ * or maxiter: their result and, when a problem was given, their certificate
+ * are stored and the slot is reused at once. No slot waits for another, and
+ * a request's arithmetic does not depend on what shares the batch with it.
+ * ---------------------------------------------------------------------- */
+typedef struct strom_batch strom_batch;
+
+int strom_batch_create(const strom_sdp* tmpl, int32_t slots, const strom_options* opt, strom_batch** out);
+void strom_batch_destroy(strom_batch* b);
+/* Copies the request. problem (nullable): certify the result on completion.
+ * X0, S0 (nullable, length nsvec): warm start of Algorithm 1.
+ * Errors: INVALID when the SDP's structure differs from the template. */
+int strom_batch_submit(strom_batch* b, const strom_sdp* sdp, const strom_problem* problem, const double* X0,
+                       const double* S0, uint64_t* ticket);
+int strom_batch_step(strom_batch* b, int32_t iters, void* stream, int32_t* n_running, int32_t* n_queued);
+/* STROM_OK once the request finished (outputs filled; c only if a problem
+ * was given), STROM_PENDING before. latency_s: submit to retirement. */
+int strom_batch_poll(strom_batch* b, uint64_t ticket, strom_result* r, strom_certificate* c, double* latency_s);
 /* ------------------------------------------------------------------------
  * Kernel-level entry points for parity tests (device pointers, caller's
  * stream). They use the solver's uploaded operator of the whole batch: x has

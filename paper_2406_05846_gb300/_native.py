@@ -7,7 +7,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libstrom.so")
 
-STROM_OK, STROM_MAXITER = 0, 1
+STROM_OK, STROM_MAXITER, STROM_PENDING = 0, 1, 2
 STROM_PREC_FP64, STROM_PREC_FP32, STROM_PREC_MIXED = 0, 1, 2
 
 
@@ -89,6 +89,12 @@ SIGNATURES = {
     "strom_kernel_A": (C.c_int, [P, P, P, P]),
     "strom_kernel_At": (C.c_int, [P, P, P, P]),
     "strom_kernel_solve": (C.c_int, [P, P, P, P]),
+    "strom_batch_create": (C.c_int, [P, C.c_int32, C.POINTER(strom_options), C.POINTER(P)]),
+    "strom_batch_destroy": (None, [P]),
+    "strom_batch_submit": (C.c_int, [P, P, P, PD, PD, C.POINTER(C.c_uint64)]),
+    "strom_batch_step": (C.c_int, [P, C.c_int32, P, PI32, PI32]),
+    "strom_batch_poll": (C.c_int, [P, C.c_uint64, C.POINTER(strom_result), C.POINTER(strom_certificate),
+                                   PD]),
     "strom_psd_plan_create": (C.c_int, [PI64, PI32, C.c_int32, C.c_int32, C.POINTER(P)]),
     "strom_psd_plan_destroy": (None, [P]),
     "strom_psd_execute": (C.c_int, [P, P, P, P, P]),

@@ -249,6 +249,50 @@ class Solver:
         check(lib().strom_kernel_solve(self.handle, r_ptr, y_ptr, stream), "strom_kernel_solve")
 
 
+class Batch:
+    """strom_batch: continuous batching of solve requests over `slots` solver slots."""
+
+    def __init__(self, template: Sdp, slots: int, **opts):
+        self.opt = default_options(**opts)
+        h = C.c_void_p()
+        check(lib().strom_batch_create(template.handle, slots, C.byref(self.opt), C.byref(h)), "strom_batch_create")
+        self.handle = h
+        self.slots = slots
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib().strom_batch_destroy(self.handle)
+            self.handle = None
+
+    def submit(self, sdp: Sdp, problem: Problem | None = None, X0=None, S0=None) -> int:
+        t = C.c_uint64()
+        px = None if X0 is None else _ptr(np.ascontiguousarray(X0, np.float64), C.c_double)
+        ps = None if S0 is None else _ptr(np.ascontiguousarray(S0, np.float64), C.c_double)
+        check(lib().strom_batch_submit(self.handle, sdp.handle, problem.handle if problem else None, px, ps,
+                                       C.byref(t)), "strom_batch_submit")
+        return t.value
+
+    def step(self, iters: int, stream=None):
+        run, q = C.c_int32(), C.c_int32()
+        check(lib().strom_batch_step(self.handle, iters, stream, C.byref(run), C.byref(q)), "strom_batch_step")
+        return run.value, q.value
+
+    def poll(self, ticket: int):
+        """None while pending, else (Result, Certificate or None, latency_s)."""
+        r, c, lat = N.strom_result(), N.strom_certificate(), C.c_double()
+        c.max_ratio = float("nan")
+        st = check(lib().strom_batch_poll(self.handle, ticket, C.byref(r), C.byref(c), C.byref(lat)),
+                   "strom_batch_poll")
+        if st == N.STROM_PENDING:
+            return None
+        res = Result(r.status, r.iterations, r.pobj, r.dobj, r.eta_p, r.eta_d, r.eta_g, r.sigma, r.m_kept)
+        cert = None
+        if c.max_ratio == c.max_ratio:
+            cert = Certificate(c.max_ratio, c.lower_bound, c.phat, c.xi, c.hmax, c.gmin, bool(c.feasible),
+                               bool(c.rank_one), bool(c.certified), None, None)
+        return res, cert, lat.value
+
+
 class PsdPlan:
     """strom_psd_plan: PSD projection of a fixed list of svec blocks."""
 

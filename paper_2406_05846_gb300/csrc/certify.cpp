@@ -134,8 +134,6 @@ std::vector<double> rollout(const Problem& p, const std::vector<double>& zbar) {
   return z;
 }
 
-namespace {
-
 // certificate of one instance from the eigen data of its blocks
 // (lamX/topX: eigenvalues ascending and top eigenvector of X's blocks,
 // lamZ: eigenvalues of Z = C - A^T y; lo[b]: offset of block b in them)
@@ -205,7 +203,6 @@ void certify_one(const Problem& p, const std::vector<int32_t>& bn, const std::ve
   if (zhat_out) std::copy(zhat.begin(), zhat.end(), zhat_out);
 }
 
-}  // namespace
 }  // namespace strom
 
 using namespace strom;

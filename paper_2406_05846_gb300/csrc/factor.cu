@@ -27,7 +27,8 @@
 namespace strom {
 namespace {
 
-constexpr int FT = 256;  // threads per factor / solve CTA
+constexpr int FT = 256;       // threads per factorisation CTA
+constexpr int SOLVE_T = 128;  // threads per chain-solve CTA
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -50,10 +51,10 @@ __device__ double sdot(const YsolveDev& d, int64_t ri, int64_t rj) {
 
 // One CTA per (instance, clique): dense lower D_k = S[G_k, G_k], its diagonal,
 // and the coupling right-hand side B_k = S[G_k, cons_{k-1}].
-__global__ void __launch_bounds__(FT) assemble_kernel(YsolveDev d) {
-  const int g = blockIdx.x;  // global group id
-  const int64_t g0 = d.grp_ptr[g];
-  const int m = (int)(d.grp_ptr[g + 1] - g0);
+__global__ void __launch_bounds__(FT) assemble_kernel(YsolveDev d, const int32_t* __restrict__ glist) {
+  const int g = glist ? glist[blockIdx.x] : blockIdx.x;  // global group id
+  const int64_t g0 = d.grp_beg[g];
+  const int m = d.grp_len[g];
   double* L = d.fac + d.fac_off[g];
   double* diag0 = d.diag0 + g0;
   for (int64_t idx = threadIdx.x; idx < (int64_t)m * m; idx += FT) {
@@ -65,8 +66,8 @@ __global__ void __launch_bounds__(FT) assemble_kernel(YsolveDev d) {
   }
   const int cprev = d.coup_n[g];
   if (cprev > 0) {
-    const int64_t pg0 = d.grp_ptr[g - 1];
-    const int pm = (int)(d.grp_ptr[g] - pg0);
+    const int64_t pg0 = d.grp_beg[g - 1];
+    const int pm = d.grp_len[g - 1];
     double* B = d.coup + d.coup_off[g];
     for (int64_t idx = threadIdx.x; idx < (int64_t)m * cprev; idx += FT) {
       const int i = (int)(idx % m), c = (int)(idx / m);
@@ -76,21 +77,20 @@ __global__ void __launch_bounds__(FT) assemble_kernel(YsolveDev d) {
 }
 
 // One CTA per instance: the chain factorisation, cliques N..1.
-__global__ void __launch_bounds__(FT) chain_factor_kernel(YsolveDev d, double rank_tol) {
-  const int inst = blockIdx.x;
+__global__ void __launch_bounds__(FT) chain_factor_kernel(YsolveDev d, double rank_tol, const int32_t* __restrict__ ilist) {
+  const int inst = ilist ? ilist[blockIdx.x] : blockIdx.x;
   const int gbeg = d.inst_grp[inst], gend = d.inst_grp[inst + 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __shared__ double s_piv;
   __shared__ int s_keep;
   for (int g = gend - 1; g >= gbeg; --g) {
-    const int64_t g0 = d.grp_ptr[g];
-    const int m = (int)(d.grp_ptr[g + 1] - g0);
+    const int64_t g0 = d.grp_beg[g];
+    const int m = d.grp_len[g];
     double* L = d.fac + d.fac_off[g];
     // Schur update from the clique factored just before: D[cons, cons] -= E^T E
     if (g + 1 < gend) {
       const int cn = d.coup_n[g + 1];
-      const int64_t ng0 = d.grp_ptr[g + 1];
-      const int nm = (int)(d.grp_ptr[g + 2] - ng0);
+      const int nm = d.grp_len[g + 1];
       const double* E = d.coup + d.coup_off[g + 1];
       for (int pair = warp; pair < cn * cn; pair += FT / 32) {
         const int a = pair % cn, b = pair / cn;
@@ -215,10 +215,17 @@ __global__ void other_rhs_kernel(YsolveDev d, const double* __restrict__ r, cons
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= d.noth) return;
   const int64_t row = d.oth_rows[q];
+  if (row < 0) return;  // unused capacity after the row reduction
   if (d.inst_active && !d.inst_active[d.row_inst[row]]) return;
   double t = r[row];
   for (int64_t e = d.rowptr[row]; e < d.rowptr[row + 1]; ++e) t += d.val[e] * rho[d.col[e]];
   yo[q] = d.keep_oth[q] ? t : 0.0;
+}
+
+// y = 0 on the rows removed by the row reduction
+__global__ void zero_rows_kernel(const int64_t* __restrict__ rows, int64_t n, double* __restrict__ y) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) y[rows[q]] = 0.0;
 }
 
 // block forward / backward substitution along the chain; one CTA per instance.
@@ -226,7 +233,7 @@ __global__ void other_rhs_kernel(YsolveDev d, const double* __restrict__ r, cons
 // solution is written back to yo and scattered to y. Each 32 x 32 diagonal
 // block is applied through its precomputed inverse (a parallel product),
 // so no step of the substitution is a sequential chain of 32 divisions.
-__global__ void __launch_bounds__(FT) chain_solve_kernel(YsolveDev d, double* __restrict__ yo, double* __restrict__ y) {
+__global__ void __launch_bounds__(SOLVE_T) chain_solve_kernel(YsolveDev d, double* __restrict__ yo, double* __restrict__ y) {
   const int inst = blockIdx.x;
   if (d.inst_active && !d.inst_active[inst]) return;
   const int gbeg = d.inst_grp[inst], gend = d.inst_grp[inst + 1];
@@ -234,17 +241,17 @@ __global__ void __launch_bounds__(FT) chain_solve_kernel(YsolveDev d, double* __
   extern __shared__ double sh[];  // [max group size]
   // forward: groups gend-1 .. gbeg,  w_g = L_g^{-1} (t_g - F_g w_{g+1})
   for (int g = gend - 1; g >= gbeg; --g) {
-    const int64_t g0 = d.grp_ptr[g];
-    const int m = (int)(d.grp_ptr[g + 1] - g0);
+    const int64_t g0 = d.grp_beg[g];
+    const int m = d.grp_len[g];
     const double* L = d.fac + d.fac_off[g];
-    for (int i = threadIdx.x; i < m; i += FT) sh[i] = yo[g0 + i];
+    for (int i = threadIdx.x; i < m; i += SOLVE_T) sh[i] = yo[g0 + i];
     __syncthreads();
     if (g + 1 < gend) {
       const int cn = d.coup_n[g + 1];
-      const int64_t ng0 = d.grp_ptr[g + 1];
-      const int nm = (int)(d.grp_ptr[g + 2] - ng0);
+      const int64_t ng0 = d.grp_beg[g + 1];
+      const int nm = d.grp_len[g + 1];
       const double* E = d.coup + d.coup_off[g + 1];
-      for (int a = warp; a < cn; a += FT / 32) {
+      for (int a = warp; a < cn; a += SOLVE_T / 32) {
         double s = 0.0;
         for (int rr = lane; rr < nm; rr += 32) s += E[(int64_t)a * nm + rr] * yo[ng0 + rr];
         s = warp_sum(s);
@@ -256,35 +263,47 @@ __global__ void __launch_bounds__(FT) chain_solve_kernel(YsolveDev d, double* __
     for (int jb = 0; jb < m; jb += 32) {
       const int je = min(jb + 32, m), bs = je - jb;
       const double* Db = Dg + (int64_t)(jb / 32) * 1024;
-      // w_b = Dinv_b t_b  (threads 0..31, column-major Dinv: coalesced)
-      double w = 0.0;
-      if (threadIdx.x < 32) {
-        const int j = threadIdx.x;
-        for (int t = 0; t < bs; ++t) w += Db[t * 32 + j] * sh[jb + t];
+      // w_b = Dinv_b t_b: warp w computes outputs j = w, w + nwarps, ...; lane t
+      // holds term t of the dot product (Dinv column-major: Dinv[t][j] at t*32+j)
+      {
+        const double tt = (lane < bs) ? sh[jb + lane] : 0.0;
+        double wv[32 / (SOLVE_T / 32)];
+#pragma unroll
+        for (int q = 0; q < 32 / (SOLVE_T / 32); ++q) {
+          const int j = warp + q * (SOLVE_T / 32);
+          const double v = (lane < bs) ? Db[lane * 32 + j] * tt : 0.0;
+          wv[q] = warp_sum(v);
+        }
+        __syncthreads();
+        if (lane == 0) {
+#pragma unroll
+          for (int q = 0; q < 32 / (SOLVE_T / 32); ++q) {
+            const int j = warp + q * (SOLVE_T / 32);
+            if (j < bs) sh[jb + j] = wv[q];
+          }
+        }
       }
       __syncthreads();
-      if (threadIdx.x < bs) sh[jb + threadIdx.x] = w;
-      __syncthreads();
-      for (int i = je + threadIdx.x; i < m; i += FT) {
+      for (int i = je + threadIdx.x; i < m; i += SOLVE_T) {
         double acc = 0.0;
         for (int jj = jb; jj < je; ++jj) acc += L[(int64_t)jj * m + i] * sh[jj];
         sh[i] -= acc;
       }
       __syncthreads();
     }
-    for (int i = threadIdx.x; i < m; i += FT) yo[g0 + i] = sh[i];
+    for (int i = threadIdx.x; i < m; i += SOLVE_T) yo[g0 + i] = sh[i];
     __syncthreads();
   }
   // backward: groups gbeg .. gend-1,  y_g = L_g^{-T} (w_g - E_g y_{g-1}[cons])
   for (int g = gbeg; g < gend; ++g) {
-    const int64_t g0 = d.grp_ptr[g];
-    const int m = (int)(d.grp_ptr[g + 1] - g0);
+    const int64_t g0 = d.grp_beg[g];
+    const int m = d.grp_len[g];
     const double* L = d.fac + d.fac_off[g];
     const double* Dg = d.dinv + d.dinv_off[g];
     const int cprev = d.coup_n[g];
     const double* E = d.coup + d.coup_off[g];
-    const int64_t pcons0 = (g > gbeg) ? d.grp_ptr[g] - cprev : 0;  // consensus rows ending group g-1
-    for (int i = threadIdx.x; i < m; i += FT) {
+    const int64_t pcons0 = (g > gbeg) ? d.grp_beg[g - 1] + d.grp_len[g - 1] - cprev : 0;  // consensus rows ending group g-1
+    for (int i = threadIdx.x; i < m; i += SOLVE_T) {
       double w = yo[g0 + i];
       for (int c = 0; c < cprev; ++c) w -= E[(int64_t)c * m + i] * yo[pcons0 + c];
       sh[i] = w;
@@ -294,7 +313,7 @@ __global__ void __launch_bounds__(FT) chain_solve_kernel(YsolveDev d, double* __
     for (int b = nb - 1; b >= 0; --b) {
       const int jb = b * 32, je = min(jb + 32, m);
       // w_j -= sum_{i >= je} L[i][j] y_i for j in [jb, je)
-      for (int j = jb + warp; j < je; j += FT / 32) {
+      for (int j = jb + warp; j < je; j += SOLVE_T / 32) {
         const double* colj = L + (int64_t)j * m;
         double s = 0.0;
         for (int i = je + lane; i < m; i += 32) s += colj[i] * sh[i];
@@ -302,18 +321,30 @@ __global__ void __launch_bounds__(FT) chain_solve_kernel(YsolveDev d, double* __
         if (lane == 0) sh[j] -= s;
       }
       __syncthreads();
-      // y_b = Dinv_b^T w_b
-      const double* Db = Dg + (int64_t)b * 1024;
-      double v = 0.0;
-      if (threadIdx.x < 32) {
-        const int j = threadIdx.x;
-        for (int t = 0; t < je - jb; ++t) v += Db[(int64_t)j * 32 + t] * sh[jb + t];
+      // y_b = Dinv_b^T w_b: output j is the dot of column j of Dinv with w_b
+      {
+        const double* Db = Dg + (int64_t)b * 1024;
+        const int bs = je - jb;
+        const double tt = (lane < bs) ? sh[jb + lane] : 0.0;
+        double wv[32 / (SOLVE_T / 32)];
+#pragma unroll
+        for (int q = 0; q < 32 / (SOLVE_T / 32); ++q) {
+          const int j = warp + q * (SOLVE_T / 32);
+          const double v = (lane < bs) ? Db[(int64_t)j * 32 + lane] * tt : 0.0;
+          wv[q] = warp_sum(v);
+        }
+        __syncthreads();
+        if (lane == 0) {
+#pragma unroll
+          for (int q = 0; q < 32 / (SOLVE_T / 32); ++q) {
+            const int j = warp + q * (SOLVE_T / 32);
+            if (j < bs) sh[jb + j] = wv[q];
+          }
+        }
       }
       __syncthreads();
-      if (threadIdx.x < je - jb) sh[jb + threadIdx.x] = v;
-      __syncthreads();
     }
-    for (int i = threadIdx.x; i < m; i += FT) {
+    for (int i = threadIdx.x; i < m; i += SOLVE_T) {
       yo[g0 + i] = sh[i];
       y[d.oth_rows[g0 + i]] = sh[i];
     }
@@ -346,11 +377,13 @@ __global__ void star_post_kernel(YsolveDev d, const double* __restrict__ r, doub
 
 }  // namespace
 
-void ysolve_factor(const YsolveDev& d, int ngroups, int ninst, double rank_tol, cudaStream_t st) {
-  assemble_kernel<<<ngroups, FT, 0, st>>>(d);
+void ysolve_factor(const YsolveDev& d, int ngroups, int ninst, double rank_tol, cudaStream_t st,
+                   const int32_t* glist, const int32_t* ilist) {
+  if (ngroups == 0 || ninst == 0) return;
+  assemble_kernel<<<ngroups, FT, 0, st>>>(d, glist);
   STROM_CUDA(cudaGetLastError());
   count_launches(1);
-  chain_factor_kernel<<<ninst, FT, 0, st>>>(d, rank_tol);
+  chain_factor_kernel<<<ninst, FT, 0, st>>>(d, rank_tol, ilist);
   STROM_CUDA(cudaGetLastError());
   count_launches(1);
 }
@@ -362,10 +395,15 @@ void ysolve_apply(const YsolveDev& d, int ninst, int max_group, const double* r,
     STROM_CUDA(cudaGetLastError());
     count_launches(1);
   }
+  if (d.ndropped > 0 && d.inst_active == nullptr) {
+    zero_rows_kernel<<<ceil_div(d.ndropped, 256), 256, 0, st>>>(d.dropped, d.ndropped, y);
+    STROM_CUDA(cudaGetLastError());
+    count_launches(1);
+  }
   other_rhs_kernel<<<ceil_div(d.noth, 256), 256, 0, st>>>(d, r, rho, d.yo);
   STROM_CUDA(cudaGetLastError());
   count_launches(1);
-  chain_solve_kernel<<<ninst, FT, sizeof(double) * max_group, st>>>(d, d.yo, y);
+  chain_solve_kernel<<<ninst, SOLVE_T, sizeof(double) * max_group, st>>>(d, d.yo, y);
   STROM_CUDA(cudaGetLastError());
   count_launches(1);
   if (d.nclass > 0) {

@@ -27,10 +27,16 @@ struct YsolveDev {
   const int32_t* star_inst;
   const double* omega;
   const double* inv_rep_s;
-  // groups of other rows: grp_ptr over all (instance, clique) groups
-  int64_t noth;
+  // groups of other rows, one per (instance, clique). Group g owns the
+  // entries [grp_beg[g], grp_beg[g] + capacity) of oth_rows; its first
+  // grp_len[g] entries are its rows (all of them before the row reduction,
+  // the kept ones after it) and the rest hold -1.
+  int64_t noth;              // capacity of oth_rows
   const int64_t* oth_rows;
-  const int64_t* grp_ptr;
+  const int64_t* grp_beg;
+  const int32_t* grp_len;
+  const int64_t* dropped;    // rows removed by the row reduction (y = 0 there)
+  int64_t ndropped;
   const int32_t* inst_grp;   // [ninst+1] first group of each instance
   const int32_t* coup_n;     // [ngroups] consensus rows of the previous group coupled to this one
   // factor storage
@@ -48,7 +54,9 @@ struct YsolveDev {
   const uint8_t* inst_active;  // nullable
 };
 
-void ysolve_factor(const YsolveDev& d, int ngroups, int ninst, double rank_tol, cudaStream_t st);
+// glist / ilist (device, nullable): factorise only these groups / instances
+void ysolve_factor(const YsolveDev& d, int ngroups, int ninst, double rank_tol, cudaStream_t st,
+                   const int32_t* glist = nullptr, const int32_t* ilist = nullptr);
 void ysolve_apply(const YsolveDev& d, int ninst, int max_group, const double* r, double* y, double* rho,
                   cudaStream_t st);
 

@@ -66,6 +66,12 @@ struct Sdp {
 
 Sdp* build_relaxation(const Problem& p);  // throws std::runtime_error
 
+// certificate of one instance from the eigen data of its blocks (certify.cpp)
+void certify_one(const Problem& p, const std::vector<int32_t>& bn, const std::vector<int8_t>& bk,
+                 const std::vector<int32_t>& bc, const int64_t* lo, const double* lamX, const double* topX,
+                 const double* lamZ, double by, double rank_tol, double xi_tol, strom_certificate* out,
+                 double* zbar_out, double* zhat_out);
+
 std::vector<std::vector<uint8_t>> monomial_basis(int nv, int d);
 
 }  // namespace strom

@@ -17,55 +17,13 @@ namespace strom {
 void build_classes(const int32_t* blk_n, int nblk, std::vector<int32_t>& list, PsdClasses& c);
 }
 
+#include "solver_impl.cuh"
+
 using namespace strom;
 
 namespace {
 constexpr int64_t kChunk = 4096;
-
-struct InstMeta {
-  int N, nv, dx, du;
-  int64_t nsvec, m;
-  std::vector<int32_t> block_n, block_clique;
-  std::vector<int64_t> block_off;  // local
-  std::vector<int8_t> block_kind;
-  std::vector<double> b;
-};
 }  // namespace
-
-struct strom_solver {
-  strom_options opt{};
-  int ninst = 0;
-  std::vector<InstMeta> meta;
-  std::vector<int64_t> svec_off, row_off;  // [ninst+1]
-  int64_t nsvec = 0, m = 0;
-  int nblk = 0, ngroups = 0, max_group = 0;
-  std::vector<int64_t> inst_blk_off;  // [ninst+1] first global block of instance
-  std::vector<int64_t> m_kept;
-  // device data
-  DevBuf<int64_t> rowptr, atptr, star_rep, star_row, oth_rows, grp_ptr, fac_off, coup_off, blk_off, lam_off;
-  DevBuf<int32_t> col, atrow, row_inst, star_ptr, star_inst, inst_grp, coup_n, blk_n, blk_list, blk_inst;
-  DevBuf<int32_t> inst_svec_chunk, inst_row_chunk, iters, n_active;
-  DevBuf<double> val, atval, b, C, omega, inv_rep_s, star_c, star_d, star_inv_s2, fac, coup, diag0;
-  DevBuf<double> X, S, Xb, y, yh, r, rho, norm_b, norm_C, sigma, stats, part_svec, part_rows, blk_inv_sigma;
-  DevBuf<double> vscratch, tmp_svec, lam, topvec, yo, inv_piv, dinv;
-  DevBuf<int64_t> dinv_off;
-  DevBuf<int8_t> row_kind;
-  DevBuf<uint8_t> keep, keep_oth, inst_active, inst_flag, inst_prec, blk_act32, blk_act64;
-  DevBuf<Chunk> svec_chunks, row_chunks;
-  PsdClasses cls;
-  YsolveDev yd{};
-  AdmmDev ad{};
-  AdmmParams prm{};
-  cudaStream_t stream = nullptr;
-  cudaGraphExec_t graph = nullptr;
-  cudaGraph_t graph_def = nullptr;
-  int64_t graph_kernels = 0;  // kernel nodes of one captured iteration
-  ~strom_solver() {
-    if (graph) cudaGraphExecDestroy(graph);
-    if (graph_def) cudaGraphDestroy(graph_def);
-    if (stream) cudaStreamDestroy(stream);
-  }
-};
 
 namespace {
 
@@ -172,20 +130,10 @@ void reset_state(strom_solver* s) {
 // row reduction + factorisation of A A^T from the device data, ||b_K|| per
 // instance, and a fresh state
 void refactor(strom_solver* s) {
-  cudaStream_t st = s->stream;
-  ysolve_factor(s->yd, s->ngroups, s->ninst, s->opt.rank_tol, st);
-  std::vector<uint8_t> keep(s->m);
-  copy_d2h(keep.data(), s->keep.p, s->m, st);
-  STROM_CUDA(cudaStreamSynchronize(st));
-  std::vector<double> nb(s->ninst, 0.0);
+  std::vector<int> all(s->ninst);
+  for (int i = 0; i < s->ninst; ++i) all[i] = i;
   s->m_kept.assign(s->ninst, 0);
-  for (int i = 0; i < s->ninst; ++i) {
-    const auto& b = s->meta[i].b;
-    for (int64_t r = 0; r < (int64_t)b.size(); ++r)
-      if (keep[s->row_off[i] + r]) { nb[i] += b[r] * b[r]; s->m_kept[i]++; }
-    nb[i] = std::sqrt(nb[i]);
-  }
-  copy_h2d(s->norm_b.p, nb.data(), sizeof(double) * s->ninst, st);
+  factor_instances(s, all);
   reset_state(s);
 }
 
@@ -202,7 +150,7 @@ void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
   s->m = s->row_off[count];
   if (s->nsvec > INT32_MAX || s->m > INT32_MAX) throw StatusError(STROM_ERR_INVALID, "batch too large for int32 indices");
   // ---- concatenated host arrays
-  std::vector<int64_t> dinv_off, rowptr(1, 0), star_rep, star_row, oth_rows, grp_ptr(1, 0), fac_off(1, 0), coup_off(1, 0), blk_off,
+  std::vector<int64_t> dinv_off, rowptr(1, 0), star_rep, star_row, oth_rows, grp_beg, fac_off(1, 0), coup_off(1, 0), blk_off,
       lam_off;
   std::vector<int32_t> col, row_inst, star_ptr, star_inst, inst_grp(1, 0), coup_n, blk_n, blk_inst;
   std::vector<double> val, b, C, omega, inv_rep_s, star_c, star_d, star_inv_s2;
@@ -250,7 +198,9 @@ void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
     for (int64_t r : q.oth_rows) oth_rows.push_back(r + ro);
     for (int k = 0; k < q.N; ++k) {
       const int64_t mk = q.grp_ptr[k + 1] - q.grp_ptr[k];
-      grp_ptr.push_back(oth0 + q.grp_ptr[k + 1]);
+      grp_beg.push_back(oth0 + q.grp_ptr[k]);
+      s->grp_full_len.push_back((int32_t)mk);
+      s->grp_full_cons.push_back(q.grp_cons[k]);
       const int cprev = (k > 0) ? q.grp_cons[k - 1] : 0;
       coup_n.push_back(cprev);
       fac_off.push_back(fac_off.back() + mk * mk);
@@ -259,7 +209,8 @@ void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
       coup_off.push_back(coup_off.back() + mk * cprev);
       s->max_group = std::max<int>(s->max_group, (int)mk);
     }
-    inst_grp.push_back((int32_t)(grp_ptr.size() - 1));
+    inst_grp.push_back((int32_t)grp_beg.size());
+    s->inst_nnz_off.push_back((int64_t)val.size());
     s->inst_blk_off[i] = (int64_t)blk_n.size();
     for (size_t k = 0; k < q.block_n.size(); ++k) {
       blk_off.push_back(q.block_off[k] + so);
@@ -270,9 +221,16 @@ void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
     }
   }
   s->inst_blk_off[count] = (int64_t)blk_n.size();
+  s->inst_nnz_off.insert(s->inst_nnz_off.begin(), 0);
+  s->inst_grp_h = inst_grp;
   star_ptr.push_back((int32_t)star_row.size());
   s->nblk = (int)blk_n.size();
-  s->ngroups = (int)grp_ptr.size() - 1;
+  s->ngroups = (int)grp_beg.size();
+  s->full_oth = oth_rows;
+  s->grp_beg_h = grp_beg;
+  s->grp_len_h = s->grp_full_len;
+  s->coup_n_h = coup_n;
+  s->dropped_h.assign(count, {});
   // ---- A^T (CSR over svec positions, rows ascending)
   std::vector<int64_t> atptr(s->nsvec + 1, 0);
   for (int32_t c : col) atptr[c + 1]++;
@@ -318,7 +276,8 @@ void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
   s->star_inv_s2.upload(star_inv_s2.data(), star_inv_s2.size(), st);
   s->star_inst.upload(star_inst.data(), star_inst.size(), st);
   s->oth_rows.upload(oth_rows.data(), oth_rows.size(), st);
-  s->grp_ptr.upload(grp_ptr.data(), grp_ptr.size(), st);
+  s->grp_beg.upload(grp_beg.data(), grp_beg.size(), st);
+  s->grp_len.upload(s->grp_full_len.data(), s->grp_full_len.size(), st);
   s->inst_grp.upload(inst_grp.data(), inst_grp.size(), st);
   s->coup_n.upload(coup_n.data(), coup_n.size(), st);
   s->fac_off.upload(fac_off.data(), fac_off.size(), st);
@@ -372,7 +331,8 @@ void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
   yd.star_rep = s->star_rep.p; yd.star_c = s->star_c.p; yd.star_d = s->star_d.p; yd.star_ptr = s->star_ptr.p;
   yd.star_row = s->star_row.p; yd.star_inv_s2 = s->star_inv_s2.p; yd.star_inst = s->star_inst.p;
   yd.omega = s->omega.p; yd.inv_rep_s = s->inv_rep_s.p;
-  yd.noth = (int64_t)oth_rows.size(); yd.oth_rows = s->oth_rows.p; yd.grp_ptr = s->grp_ptr.p;
+  yd.noth = (int64_t)oth_rows.size(); yd.oth_rows = s->oth_rows.p; yd.grp_beg = s->grp_beg.p; yd.grp_len = s->grp_len.p;
+  yd.dropped = nullptr; yd.ndropped = 0;
   yd.inst_grp = s->inst_grp.p; yd.coup_n = s->coup_n.p;
   yd.fac = s->fac.p; yd.fac_off = s->fac_off.p; yd.coup = s->coup.p; yd.coup_off = s->coup_off.p;
   yd.diag0 = s->diag0.p; yd.keep = s->keep.p; yd.keep_oth = s->keep_oth.p; yd.yo = s->yo.p; yd.inv_piv = s->inv_piv.p; yd.dinv = s->dinv.p; yd.dinv_off = s->dinv_off.p;
@@ -456,39 +416,167 @@ extern "C" int strom_solver_offsets(const strom_solver* s, int32_t i, int64_t* s
   });
 }
 
+int strom::run_iterations(strom_solver* s, int iters, cudaStream_t user, int32_t* n_active) {
+  build_graph(s);
+  if (user) {  // order after the caller's prior work
+    cudaEvent_t ev;
+    STROM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    STROM_CUDA(cudaEventRecord(ev, user));
+    STROM_CUDA(cudaStreamWaitEvent(s->stream, ev, 0));
+    STROM_CUDA(cudaEventDestroy(ev));
+  }
+  int32_t act = 1;
+  int done = 0;
+  while (done < iters) {
+    const int n = std::min(iters - done, s->opt.check_every);
+    for (int k = 0; k < n; ++k) STROM_CUDA(cudaGraphLaunch(s->graph, s->stream));
+    count_launches(s->graph_kernels * n);
+    done += n;
+    copy_d2h(&act, s->n_active.p, sizeof(int32_t), s->stream);
+    STROM_CUDA(cudaStreamSynchronize(s->stream));
+    if (act == 0) break;
+  }
+  if (user) {
+    cudaEvent_t ev;
+    STROM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    STROM_CUDA(cudaEventRecord(ev, s->stream));
+    STROM_CUDA(cudaStreamWaitEvent(user, ev, 0));
+    STROM_CUDA(cudaEventDestroy(ev));
+  }
+  if (n_active) *n_active = act;
+  return done;
+}
+
 extern "C" int strom_solver_step(strom_solver* s, int32_t iters, void* stream, int32_t* n_active) {
   return guard([&] {
     if (!s || iters < 0) throw StatusError(STROM_ERR_INVALID, "strom_solver_step: bad arguments");
-    cudaStream_t user = (cudaStream_t)stream;
-    build_graph(s);
-    if (user) {  // order after the caller's prior work
-      cudaEvent_t ev;
-      STROM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-      STROM_CUDA(cudaEventRecord(ev, user));
-      STROM_CUDA(cudaStreamWaitEvent(s->stream, ev, 0));
-      STROM_CUDA(cudaEventDestroy(ev));
-    }
-    int32_t act = 1;
-    int done = 0;
-    while (done < iters) {
-      const int n = std::min(iters - done, s->opt.check_every);
-      for (int k = 0; k < n; ++k) STROM_CUDA(cudaGraphLaunch(s->graph, s->stream));
-      count_launches(s->graph_kernels * n);
-      done += n;
-      copy_d2h(&act, s->n_active.p, sizeof(int32_t), s->stream);
-      STROM_CUDA(cudaStreamSynchronize(s->stream));
-      if (act == 0) break;
-    }
-    if (user) {
-      cudaEvent_t ev;
-      STROM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-      STROM_CUDA(cudaEventRecord(ev, s->stream));
-      STROM_CUDA(cudaStreamWaitEvent(user, ev, 0));
-      STROM_CUDA(cudaEventDestroy(ev));
-    }
-    if (n_active) *n_active = act;
+    run_iterations(s, iters, (cudaStream_t)stream, n_active);
     return STROM_OK;
   });
+}
+
+// upload the group lists (oth_rows slices, lengths, coupling counts) of a set
+// of instances from the host copies
+static void upload_groups(strom_solver* s, const std::vector<int>& inst, const std::vector<int64_t>& oth) {
+  for (int i : inst) {
+    const int g0 = s->inst_grp_h[i], g1 = s->inst_grp_h[i + 1];
+    const int64_t b0 = s->grp_beg_h[g0];
+    const int64_t b1 = s->grp_beg_h[g1 - 1] + s->grp_full_len[g1 - 1];
+    copy_h2d(s->oth_rows.p + b0, oth.data() + b0, sizeof(int64_t) * (b1 - b0), s->stream);
+    copy_h2d(s->grp_len.p + g0, s->grp_len_h.data() + g0, sizeof(int32_t) * (g1 - g0), s->stream);
+    copy_h2d(s->coup_n.p + g0, s->coup_n_h.data() + g0, sizeof(int32_t) * (g1 - g0), s->stream);
+  }
+}
+
+// Factorise a subset of instances. Pass 1 runs the pivot-skipping Cholesky on
+// all other rows and decides which rows are dependent; pass 2 factorises
+// again on the kept rows only, so the triangular solves of every iteration
+// carry no dropped rows. Each group keeps its full-size storage, so one
+// instance can be refactorised without moving the others.
+void strom::factor_instances(strom_solver* s, const std::vector<int>& inst) {
+  if (inst.empty()) return;
+  std::vector<int32_t> gl, il(inst.begin(), inst.end());
+  for (int i : inst)
+    for (int g = s->inst_grp_h[i]; g < s->inst_grp_h[i + 1]; ++g) gl.push_back(g);
+  DevBuf<int32_t> gd, id;
+  gd.upload(gl.data(), gl.size(), s->stream);
+  id.upload(il.data(), il.size(), s->stream);
+  // pass 1: full groups
+  for (int i : inst)
+    for (int g = s->inst_grp_h[i]; g < s->inst_grp_h[i + 1]; ++g) {
+      s->grp_len_h[g] = s->grp_full_len[g];
+      s->coup_n_h[g] = (g > s->inst_grp_h[i]) ? s->grp_full_cons[g - 1] : 0;
+    }
+  upload_groups(s, inst, s->full_oth);
+  for (int i : inst) {  // rows of these instances start as kept
+    const int64_t ro = s->row_off[i], m = s->row_off[i + 1] - ro;
+    STROM_CUDA(cudaMemsetAsync(s->keep.p + ro, 1, m, s->stream));
+  }
+  ysolve_factor(s->yd, (int)gl.size(), (int)il.size(), s->opt.rank_tol, s->stream, gd.p, id.p);
+  std::vector<uint8_t> keep(s->m);
+  copy_d2h(keep.data(), s->keep.p, s->m, s->stream);
+  STROM_CUDA(cudaStreamSynchronize(s->stream));
+  // pass 2: kept rows only
+  std::vector<int64_t> oth(s->full_oth.size(), -1);
+  std::vector<int32_t> kept_cons(s->ngroups, 0);
+  for (int i : inst) {
+    s->dropped_h[i].clear();
+    for (int g = s->inst_grp_h[i]; g < s->inst_grp_h[i + 1]; ++g) {
+      const int64_t b = s->grp_beg_h[g];
+      const int L = s->grp_full_len[g], C = s->grp_full_cons[g];
+      int len = 0, cons = 0;
+      for (int q = 0; q < L; ++q) {
+        const int64_t row = s->full_oth[b + q];
+        if (keep[row]) {
+          oth[b + len++] = row;
+          if (q >= L - C) ++cons;
+        } else {
+          s->dropped_h[i].push_back(row);
+        }
+      }
+      s->grp_len_h[g] = len;
+      kept_cons[g] = cons;
+    }
+    for (int g = s->inst_grp_h[i]; g < s->inst_grp_h[i + 1]; ++g)
+      s->coup_n_h[g] = (g > s->inst_grp_h[i]) ? kept_cons[g - 1] : 0;
+  }
+  upload_groups(s, inst, oth);
+  ysolve_factor(s->yd, (int)gl.size(), (int)il.size(), s->opt.rank_tol, s->stream, gd.p, id.p);
+  // rows removed by the reduction, all instances
+  std::vector<int64_t> dr;
+  for (const auto& v : s->dropped_h) dr.insert(dr.end(), v.begin(), v.end());
+  s->dropped.upload(dr.data(), dr.size(), s->stream);
+  s->yd.dropped = s->dropped.p;
+  s->yd.ndropped = (int64_t)dr.size();
+  // ||b_K|| and |K| of the refactorised instances
+  std::vector<double> nb(s->ninst);
+  copy_d2h(nb.data(), s->norm_b.p, sizeof(double) * s->ninst, s->stream);
+  STROM_CUDA(cudaStreamSynchronize(s->stream));
+  for (int i : inst) {
+    const auto& bv = s->meta[i].b;
+    double acc = 0.0;
+    int64_t kept = 0;
+    for (int64_t r = 0; r < (int64_t)bv.size(); ++r)
+      if (keep[s->row_off[i] + r]) { acc += bv[r] * bv[r]; ++kept; }
+    nb[i] = std::sqrt(acc);
+    s->m_kept[i] = kept;
+  }
+  copy_h2d(s->norm_b.p, nb.data(), sizeof(double) * s->ninst, s->stream);
+  STROM_CUDA(cudaStreamSynchronize(s->stream));
+}
+
+// X = S = y = 0, sigma = sigma0, active, iteration count 0, for a set of instances
+void strom::reset_instances(strom_solver* s, const std::vector<int>& inst) {
+  cudaStream_t st = s->stream;
+  std::vector<double> sg(s->ninst);
+  std::vector<uint8_t> act(s->ninst), flag(s->ninst), prec(s->ninst);
+  std::vector<int32_t> it(s->ninst);
+  copy_d2h(sg.data(), s->sigma.p, sizeof(double) * s->ninst, st);
+  copy_d2h(act.data(), s->inst_active.p, s->ninst, st);
+  copy_d2h(flag.data(), s->inst_flag.p, s->ninst, st);
+  copy_d2h(prec.data(), s->inst_prec.p, s->ninst, st);
+  copy_d2h(it.data(), s->iters.p, sizeof(int32_t) * s->ninst, st);
+  STROM_CUDA(cudaStreamSynchronize(st));
+  const uint8_t p0 = (uint8_t)(s->opt.precision == STROM_PREC_FP64 ? STROM_PREC_FP64 : STROM_PREC_FP32);
+  for (int i : inst) {
+    const int64_t so = s->svec_off[i], n = s->svec_off[i + 1] - so;
+    const int64_t ro = s->row_off[i], m = s->row_off[i + 1] - ro;
+    STROM_CUDA(cudaMemsetAsync(s->X.p + so, 0, n * sizeof(double), st));
+    STROM_CUDA(cudaMemsetAsync(s->S.p + so, 0, n * sizeof(double), st));
+    STROM_CUDA(cudaMemsetAsync(s->y.p + ro, 0, m * sizeof(double), st));
+    STROM_CUDA(cudaMemsetAsync(s->yh.p + ro, 0, m * sizeof(double), st));
+    sg[i] = s->opt.sigma0;
+    act[i] = 1;
+    flag[i] = 0;
+    prec[i] = p0;
+    it[i] = 0;
+  }
+  copy_h2d(s->sigma.p, sg.data(), sizeof(double) * s->ninst, st);
+  copy_h2d(s->inst_active.p, act.data(), s->ninst, st);
+  copy_h2d(s->inst_flag.p, flag.data(), s->ninst, st);
+  copy_h2d(s->inst_prec.p, prec.data(), s->ninst, st);
+  copy_h2d(s->iters.p, it.data(), sizeof(int32_t) * s->ninst, st);
+  STROM_CUDA(cudaStreamSynchronize(st));
 }
 
 extern "C" int strom_solver_factor(strom_solver* s, void* stream) {
@@ -659,6 +747,60 @@ __global__ void z_kernel(const int64_t* atptr, const int32_t* atrow, const doubl
   Z[p] = C[p] - acc;
 }
 }  // namespace
+
+// eigenvalues (ascending) and top eigenvectors of the blocks of a set of
+// instances, for X or Z = C - A^T y; lam_off receives the global offsets
+void strom::eig_instances(strom_solver* s, const std::vector<int>& inst, bool use_Z, std::vector<double>& lam,
+                          std::vector<double>& topvec, std::vector<int64_t>& lam_off) {
+  const double* in = s->X.p;
+  if (use_Z) {
+    for (int i : inst) {
+      const int64_t so = s->svec_off[i], se = s->svec_off[i + 1];
+      z_kernel<<<ceil_div(se - so, 256), 256, 0, s->stream>>>(s->atptr.p, s->atrow.p, s->atval.p, s->y.p, s->C.p, so,
+                                                            se, s->tmp_svec.p);
+      STROM_CUDA(cudaGetLastError());
+      count_launches(1);
+    }
+    in = s->tmp_svec.p;
+  }
+  std::vector<int32_t> nall(s->nblk);
+  copy_d2h(nall.data(), s->blk_n.p, sizeof(int32_t) * s->nblk, s->stream);
+  STROM_CUDA(cudaStreamSynchronize(s->stream));
+  PsdClasses cls;
+  std::vector<std::vector<int32_t>> per(4);
+  for (int i : inst)
+    for (int64_t b = s->inst_blk_off[i]; b < s->inst_blk_off[i + 1]; ++b) {
+      const int n = nall[b];
+      per[n <= 16 ? 0 : n <= 40 ? 1 : n <= 80 ? 2 : 3].push_back((int32_t)b);
+    }
+  std::vector<int32_t> ids;
+  for (int k = 0; k < 4; ++k) {
+    cls.start[k] = (int)ids.size();
+    cls.count[k] = (int)per[k].size();
+    for (int b : per[k]) ids.push_back(b);
+  }
+  DevBuf<int32_t> list;
+  list.upload(ids.data(), ids.size(), s->stream);
+  DevBuf<double> vs;
+  if (cls.count[3] > 0) vs.alloc((size_t)cls.count[3] * 160 * 161);
+  PsdArgs a{};
+  a.Xb = in;
+  a.blk_off = s->blk_off.p;
+  a.blk_n = s->blk_n.p;
+  a.blk_list = list.p;
+  a.lam = s->lam.p;
+  a.lam_off = s->lam_off.p;
+  a.topvec = s->topvec.p;
+  a.vscratch = vs.p;
+  psd_launch(a, cls, STROM_PREC_FP64, s->stream);
+  lam.assign(s->lam.n, 0.0);
+  topvec.assign(s->topvec.n, 0.0);
+  lam_off.assign(s->nblk, 0);
+  copy_d2h(lam.data(), s->lam.p, sizeof(double) * lam.size(), s->stream);
+  copy_d2h(topvec.data(), s->topvec.p, sizeof(double) * topvec.size(), s->stream);
+  copy_d2h(lam_off.data(), s->lam_off.p, sizeof(int64_t) * s->nblk, s->stream);
+  STROM_CUDA(cudaStreamSynchronize(s->stream));
+}
 
 // eigenvalues (ascending, per block) and top eigenvectors of instance `inst`
 // for X (use_Z = false) or Z = C - A^T y (use_Z = true); FP64 Jacobi on the GPU
