@@ -2,18 +2,21 @@
 """Throughput of the STROM hot path on GB300: certified solves per second.
 
 Workload: pendulum swing-up, horizon N = 10, dt = 0.1, start angle
-theta0 ~ U(-0.2, 0.2) rad (seeded, instance i uses seed 20240607 + i), a
-batch of B independent instances. One step = the whole hot path on the batch:
-row reduction + factorisation of A A^T (setup), sGS-ADMM (Algorithm 1) until
-every instance reaches max(eta_p, eta_d, eta_g) <= 1e-6 or maxiter, and the
-certificate (rank-1 test, rollout, valid lower bound, xi) of every instance.
-A solve counts when it converged and its certificate is computed.
+theta0 ~ U(-0.2, 0.2) rad (seeded: request i uses seed 20240607 + i), served
+by continuous batching over B solver slots. Every request runs the whole hot
+path: row reduction + factorisation of A A^T for its slot (setup),
+sGS-ADMM (Algorithm 1) until max(eta_p, eta_d, eta_g) <= 1e-6, and the
+certificate (rank-1 test, rollout, valid lower bound, xi). One step = a fixed
+number of iterations of the served batch (requests admitted and retired as
+slots free up). A solve counts when it converged and its certificate was
+computed.
 
-  value : SDP data resident in HBM when the timed region starts
-  e2e   : through the public API from host polynomial data (relaxation,
-          upload, factorisation, solve, certificate, results to host)
-  plain : the same instances one at a time with the FP64 eigensolver
-          (the plain single-instance form), for comparison
+  value : steady-state served throughput after the warm-up steps, requests
+          queued before timing
+  e2e   : the same batch continued, each step building (relaxation from
+          polynomial data) and submitting its replacement requests inside the
+          timed region and reading every result on the host
+  plain : single instances one at a time with the FP64 eigensolver
 
 Multi-GPU: replicas only (independent batches per rank, no collective on the
 data path); value = certified solves of all ranks / max time over ranks.
@@ -41,11 +44,19 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="strom", choices=["strom", "reference"])
-    ap.add_argument("--batch", type=int, default=512)
+    ap.add_argument("--slots", type=int, default=512)
+    ap.add_argument("--iters", type=int, default=800, help="sGS-ADMM iterations per step")
     ap.add_argument("--horizon", type=int, default=10)
     ap.add_argument("--maxiter", type=int, default=6000)
-    ap.add_argument("--plain", type=int, default=2, help="instances timed in the plain FP64 single-instance form")
+    ap.add_argument("--plain", type=int, default=1, help="instances timed in the plain FP64 single-instance form")
     ap.add_argument("--cpu-budget", type=float, default=25.0)
+    ap.add_argument("--workload", default="served", choices=["served", "psd"],
+                    help="served: certified solves/s (default); psd: the 4096-block PSD-projection microbench")
+    ap.add_argument("--profile", default="none", choices=["none", "iterations", "psd"],
+                    help="run a few launches of one case and exit (for ncu captures); prints no JSON")
+    ap.add_argument("--precision", type=int, default=1, help="psd workload / profile: 0 = FP64, 1 = FP32")
+    ap.add_argument("--polish-eta", type=float, default=1e-6,
+                    help="switch an instance to the FP64 eigensolver once eta <= this (FP32 before)")
     return ap.parse_args()
 
 
@@ -120,16 +131,22 @@ def relax_all(S, problems):
 
 
 def chain_solve_flops(sdp, keep):
-    """FP64 flops of one block-banded y-solve (forward + backward) per instance."""
+    """FP64 flops of one block-banded y-solve (forward + backward) of one instance.
+
+    The triangular factors cover the rows kept by the row reduction that are
+    not moment-duplication rows: per clique group of m rows, m (m + 1) / 2
+    multiply-adds forward and again backward, plus the coupling with the
+    previous group's c kept consensus rows (m c each way).
+    """
     import numpy as np
     a = sdp.export()
-    oth = a.row_kind != 0
+    oth = (a.row_kind != 0) & keep
     flops = 0
     prev_c = 0
     for k in range(int(a.row_clique.max()) + 1):
         rows = oth & (a.row_clique == k)
         m = int(rows.sum())
-        cons = int(np.sum((a.row_kind == 4) & (a.row_clique == k)))
+        cons = int(np.sum((a.row_kind == 4) & (a.row_clique == k) & keep))
         flops += 2 * (m * (m + 1) + 2 * m * prev_c)
         prev_c = cons
     return flops
@@ -138,6 +155,23 @@ def chain_solve_flops(sdp, keep):
 def psd_flops(sizes, r_frac=0.7):
     """W(n) = 9 n^3 + 2 n^2 r per block (symmetric eigendecomposition + recombination)."""
     return sum(9 * n ** 3 + 2 * n * n * (r_frac * n) for n in sizes)
+
+
+class Feeder:
+    """Seeded pendulum requests, relaxed by the library's builder in worker threads."""
+
+    def __init__(self, S, N, seed0):
+        self.S, self.N, self.next = S, N, seed0
+
+    def take(self, k):
+        import numpy as np
+        import workloads as wl
+        probs = []
+        for i in range(k):
+            rng = np.random.default_rng(np.random.PCG64(self.next + i))
+            probs.append(wl.pendulum_problem(N=self.N, theta0=float(rng.uniform(-0.2, 0.2))))
+        self.next += k
+        return relax_all(self.S, probs)
 
 
 def run_strom(a, rank, world):
@@ -152,24 +186,35 @@ def run_strom(a, rank, world):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     S.lib()
-    B, N = a.batch, a.horizon
-    problems = make_problems(B, N, rank * B)
-    P, sdps = relax_all(S, problems)
-    solver = S.Solver(sdps, tol=1e-6, maxiter=a.maxiter, precision=S.STROM_PREC_MIXED, polish_eta=1e-5,
-                      check_every=25)
+    B, N, it = a.slots, a.horizon, a.iters
+    feed = Feeder(S, N, SEED + rank * 10_000_000)
+    P0, sd0 = feed.take(1)
+    opts = dict(tol=1e-6, maxiter=a.maxiter, precision=S.STROM_PREC_MIXED, polish_eta=a.polish_eta,
+                check_every=a.iters)
+    batch = S.Batch(sd0[0], B, **opts)
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
+    # requests for the whole run, queued in host memory before timing (their
+    # A, b, C values are uploaded at admission, inside the timed region)
+    per_step = max(1, int(B * it / 1200))      # expected retirements per step (about 2000 iterations each)
+    total = B + (a.warmup + a.steps + 1) * per_step
+    outstanding = []
+    while len(outstanding) < total:
+        k = min(512, total - len(outstanding))
+        P, sd = feed.take(k)
+        outstanding += [batch.submit(x, pr) for x, pr in zip(sd, P)]
+        del P, sd
 
-    def step():
-        solver.factor(sp)
-        solver.solve(sp)
-        certs = solver.certify_batch(P)
-        res = [solver.result(i) for i in range(B)]
-        ok = [r.status == S.STROM_OK and c.xi == c.xi for r, c in zip(res, certs)]
-        return sum(ok), res, certs
+    def harvest(tickets):
+        done, keep = [], []
+        for t in tickets:
+            o = batch.poll(t, with_service=True)
+            (keep if o is None else done).append(t if o is None else o)
+        return done, keep
 
     for _ in range(a.warmup):
-        step()
+        batch.step(it, sp)
+    _, outstanding = harvest(outstanding)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -179,19 +224,18 @@ def run_strom(a, rank, world):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    solved = 0
-    iters = []
-    certified_flag = 0
+    finished = []
     for _ in range(a.steps):
-        n, res, certs = step()
-        solved += n
-        iters += [r.iterations for r in res]
-        certified_flag += sum(c.certified for c in certs)
+        batch.step(it, sp)
+        d, outstanding = harvest(outstanding)
+        finished += d
     e1.record(stream)
     torch.cuda.synchronize()
     launches = S.launch_count() - l0
     clocks = clk.stop()
     t = e0.elapsed_time(e1) / 1e3
+    ok = [f for f in finished if f[0].status == S.STROM_OK and f[1] is not None and f[1].xi == f[1].xi]
+    solved = len(ok)
     if dist:
         tt = torch.tensor([t], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -200,68 +244,74 @@ def run_strom(a, rank, world):
         dist.all_reduce(ss)
         solved = int(ss.item())
     value = solved / t
+    svc = np.array([f[3] for f in ok]) if ok else np.array([np.nan])
+    iters = np.array([f[0].iterations for f in ok]) if ok else np.array([0])
+    cert_frac = float(np.mean([f[1].certified for f in ok])) if ok else 0.0
 
-    # ---- end to end from host polynomial data, through the public API
+    # ---- end to end through the public API, continuing the same warmed batch:
+    # each step builds its replacement requests from polynomial data
+    # (relaxation), submits them, serves, and reads the results on the host
     h2d0, d2h0 = S.transfer_bytes()
-    host_out = 0
     te0 = time.perf_counter()
-    e2e_solved = 0
+    e2e_done = 0
     for _ in range(a.steps):
-        P2, sd2 = relax_all(S, problems)
-        s2 = S.Solver(sd2, tol=1e-6, maxiter=a.maxiter, precision=S.STROM_PREC_MIXED, polish_eta=1e-5,
-                      check_every=25)
-        s2.solve()
-        c2 = s2.certify_batch(P2)
-        r2 = [s2.result(i) for i in range(B)]
-        X = [s2.state(i)[0] for i in range(B)]  # moment matrices / primal solution to host
-        e2e_solved += sum(r.status == S.STROM_OK and c.xi == c.xi for r, c in zip(r2, c2))
-        host_out += sum(x.nbytes for x in X)
-        del s2
+        P, sd = feed.take(per_step)
+        outstanding += [batch.submit(x, pr) for x, pr in zip(sd, P)]
+        del P, sd
+        batch.step(it, sp)
+        d, outstanding = harvest(outstanding)
+        e2e_done += sum(1 for f in d if f[0].status == S.STROM_OK and f[1] is not None and f[1].xi == f[1].xi)
     torch.cuda.synchronize()
     te = time.perf_counter() - te0
     h2d1, d2h1 = S.transfer_bytes()
-    e2e = {"value": e2e_solved / te, "unit": "solves/s", "h2d_bytes_per_step": (h2d1 - h2d0) // a.steps,
+    e2e = {"value": e2e_done / te, "unit": "solves/s", "h2d_bytes_per_step": (h2d1 - h2d0) // a.steps,
            "d2h_bytes_per_step": (d2h1 - d2h0) // a.steps}
+    del batch
 
-    # ---- latency of the batched form (per step) and the plain single-instance FP64 form
-    lat = []
-    plain_t = 0.0
+    # ---- the plain single-instance FP64 form on the same kind of requests
+    plain_lat = []
     plain_ok = 0
-    for i in range(min(a.plain, B)):
-        sv = S.Solver([sdps[i]], tol=1e-6, maxiter=a.maxiter, precision=S.STROM_PREC_FP64, check_every=25)
+    Pp, sdp = feed.take(a.plain)
+    for i in range(a.plain):
+        sv = S.Solver([sdp[i]], tol=1e-6, maxiter=a.maxiter, precision=S.STROM_PREC_FP64, check_every=100)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sv.factor()
         sv.solve()
-        cc = sv.certify(0, P[i])
+        sv.certify(0, Pp[i])
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        plain_t += dt
-        lat.append(dt)
+        plain_lat.append(time.perf_counter() - t0)
         plain_ok += sv.result(0).status == S.STROM_OK
-    plain = {"value": plain_ok / plain_t if plain_t > 0 else None, "unit": "solves/s",
-             "instances": min(a.plain, B), "precision": "fp64", "mode": "one instance at a time"}
+        del sv
+    plain = {"value": plain_ok / sum(plain_lat) if plain_lat else None, "unit": "solves/s",
+             "instances": a.plain, "precision": "fp64 eigensolver, fp64 y-solve", "mode": "one instance at a time",
+             "latency_s": plain_lat}
 
     # ---- roofline of the dominant kernel, timed live on this stream
-    roof = roofline(S, solver, sdps, stream)
+    Pr, sdr = feed.take(B)
+    solver = S.Solver(sdr, **opts)
+    roof = roofline(S, solver, sdr, stream)
+    del solver
     cpu = cpu_baseline(a) if (rank == 0 and world == 1) else None
     if rank == 0:
-        its = np.array(iters)
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": 1e3 * t / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
-            "config": {"workload": "pendulum swing-up N=%d dt=0.1, batch %d (theta0~U(-0.2,0.2) seeded), "
-                                   "KKT<=1e-6, FP32 Jacobi eig + FP64 polish, FP64 y-solve" % (N, B),
-                       "batch": B, "horizon": N, "maxiter": a.maxiter, "l2": "working set > L2 not guaranteed; "
-                       "every step re-factorises and restarts from X=S=0 (state rewritten each step)",
+            "config": {"workload": "pendulum swing-up N=%d dt=0.1 (theta0~U(-0.2,0.2) seeded), served by continuous "
+                                   "batching over %d slots, %d sGS-ADMM iterations per step, KKT<=1e-6, FP32 Jacobi "
+                                   "eig, FP64 Jacobi polish once eta<=%g (retirement only on an FP64 iterate), "
+                                   "FP64 y-solve, certificate per request" % (N, B, it, a.polish_eta),
+                       "slots": B, "iters_per_step": it, "horizon": N, "maxiter": a.maxiter,
+                       "inputs": "requests queued in host memory before timing; each admission uploads its A, b, C "
+                                 "values and refactorises its slot inside the timed region",
+                       "l2": "working set (about %.1f GB of slot state and factors) larger than L2" % (B * 9.0e-3),
                        "parallelism": "replicas x%d" % world},
             "e2e": e2e, "gpu_launches": launches,
-            "iterations": {"p50": float(np.percentile(its, 50)), "p99": float(np.percentile(its, 99)),
-                           "max": int(its.max())},
-            "latency_s": {"batched_step_p50": 1.0 * t / a.steps,
-                          "plain_single_p50": float(np.median(lat)) if lat else None},
-            "certified_fraction": certified_flag / max(1, B * a.steps),
+            "latency_s": {"service_p50": float(np.percentile(svc, 50)), "service_p99": float(np.percentile(svc, 99)),
+                          "plain_single_p50": float(np.median(plain_lat)) if plain_lat else None},
+            "iterations": {"p50": float(np.percentile(iters, 50)), "p99": float(np.percentile(iters, 99))},
+            "completed": len(finished), "counted": solved, "certified_fraction": cert_frac,
             "plain_fp64": plain, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
         }
         print(json.dumps(line))
@@ -403,12 +453,108 @@ def run_reference(a, rank, world):
     print(json.dumps(line))
 
 
+def run_profile(a):
+    """A few launches of one case, for ncu: 3 sGS-ADMM iterations on a batch of
+    `--slots` pendulum instances, or 3 projections of the microbench."""
+    import torch
+    import paper_2406_05846_gb300 as S
+    S.lib()
+    if a.profile == "iterations":
+        feed = Feeder(S, a.horizon, SEED)
+        _, sd = feed.take(a.slots)
+        sv = S.Solver(sd, tol=1e-6, precision=a.precision, check_every=1)
+        sv.step(3)
+    else:
+        import workloads as wl
+        x, off, n, _ = wl.psd_microbench()
+        xb = torch.tensor(x, device="cuda")
+        o = torch.zeros_like(xb)
+        plan = S.PsdPlan(off, n, a.precision)
+        for _ in range(3):
+            plan.execute(xb.data_ptr(), o.data_ptr())
+    torch.cuda.synchronize()
+
+
+def run_psd(a):
+    """The PSD-projection microbench: 4096 blocks {8: 40%, 36: 30%, 78: 20%,
+    136: 10%} with prescribed spectra, FP64 svec in and out (blocks/s)."""
+    import numpy as np
+    import torch
+    import paper_2406_05846_gb300 as S
+    import workloads as wl
+    from oracle import relax as OR
+    from oracle import sgs_admm as OA
+    S.lib()
+    x, off, n, _ = wl.psd_microbench()
+    xb = torch.tensor(x, device="cuda")
+    o = torch.zeros_like(xb)
+    plan = S.PsdPlan(off, n, a.precision)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    for _ in range(a.warmup):
+        plan.execute(xb.data_ptr(), o.data_ptr(), None, sp)
+    torch.cuda.synchronize()
+    clk = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clk.start()
+    l0 = S.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        plan.execute(xb.data_ptr(), o.data_ptr(), None, sp)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    launches = S.launch_count() - l0
+    t = e0.elapsed_time(e1) / 1e3 / a.steps
+    got = o.cpu().numpy()
+    # sampled parity against the oracle's projection (8 blocks of each size)
+    rng = np.random.default_rng(0)
+    err = 0.0
+    for k in (8, 36, 78, 136):
+        for b in rng.choice(np.nonzero(n == k)[0], 8, replace=False):
+            tt = k * (k + 1) // 2
+            X = OR.smat(x[off[b]:off[b] + tt], k)
+            err = max(err, np.linalg.norm(OR.smat(got[off[b]:off[b] + tt], k) - OA.project_block(X))
+                      / np.linalg.norm(X))
+    # end to end: host svec in, host svec out
+    h = torch.tensor(x).pin_memory()
+    ho = torch.empty_like(h).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        xb.copy_(h, non_blocking=True)
+        plan.execute(xb.data_ptr(), o.data_ptr(), None, sp)
+        ho.copy_(o, non_blocking=True)
+        torch.cuda.synchronize()
+    te = (time.perf_counter() - t0) / a.steps
+    flops = psd_flops(n.tolist())
+    fp = 75.49 if a.precision == 1 else 1.208
+    line = {"metric": "PSD projections per second (4096-block microbench)", "value": len(n) / t, "unit": "blocks/s",
+            "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if a.precision == 1 else "f64",
+            "data": "synthetic",
+            "config": {"workload": "4096 symmetric blocks {8:40%,36:30%,78:20%,136:10%}, spectra 1e-4..1 with 30% "
+                                   "negative, Haar eigenvectors, seed 1", "l2": "inputs 58 MB (fit in L2)"},
+            "e2e": {"value": len(n) / te, "unit": "blocks/s", "h2d_bytes_per_step": int(8 * len(x)),
+                    "d2h_bytes_per_step": int(8 * len(x))},
+            "gpu_launches": launches, "max_rel_error_vs_oracle": err,
+            "roofline": {"kernel": "jacobi_psd_kernel", "bound": "alu", "achieved": flops / t / 1e12, "peak": fp,
+                         "unit": "TFLOP/s", "frac": flops / t / 1e12 / fp, "traffic": None,
+                         "algorithmic_flops": flops},
+            "clocks": clocks}
+    print(json.dumps(line))
+
+
 def main():
     a = parse()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(a.gpus if a.gpus == 1 else 1)))
-    if a.impl == "reference":
+    if a.profile != "none":
+        run_profile(a)
+    elif a.impl == "reference":
         run_reference(a, rank, world)
+    elif a.workload == "psd":
+        run_psd(a)
     else:
         run_strom(a, rank, world)
 

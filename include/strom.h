@@ -127,7 +127,9 @@ typedef struct {
   double sigma_ratio, sigma_factor, sigma_min, sigma_max;
   double rank_tol;           /* relative pivot threshold of the row reduction */
   int32_t precision;         /* STROM_PREC_* */
-  double polish_eta;         /* MIXED: switch to the FP64 eigensolver once eta <= polish_eta */
+  double polish_eta;         /* MIXED: switch to the FP64 eigensolver once eta <= polish_eta; an
+                                instance meeting tol in FP32 switches too, and it retires only
+                                on an FP64 iterate with eta <= tol */
   int32_t check_every;       /* host checks for completion every this many iterations */
   double time_budget_s;      /* <= 0: none */
 } strom_options;
@@ -234,8 +236,10 @@ int strom_batch_submit(strom_batch* b, const strom_sdp* sdp, const strom_problem
                        const double* S0, uint64_t* ticket);
 int strom_batch_step(strom_batch* b, int32_t iters, void* stream, int32_t* n_running, int32_t* n_queued);
 /* STROM_OK once the request finished (outputs filled; c only if a problem
- * was given), STROM_PENDING before. latency_s: submit to retirement. */
-int strom_batch_poll(strom_batch* b, uint64_t ticket, strom_result* r, strom_certificate* c, double* latency_s);
+ * was given), STROM_PENDING before. latency_s: submit to retirement;
+ * service_s: admission into a slot to retirement. Any output may be NULL. */
+int strom_batch_poll(strom_batch* b, uint64_t ticket, strom_result* r, strom_certificate* c, double* latency_s,
+                     double* service_s);
 /* ------------------------------------------------------------------------
  * Kernel-level entry points for parity tests (device pointers, caller's
  * stream). They use the solver's uploaded operator of the whole batch: x has

@@ -94,7 +94,7 @@ SIGNATURES = {
     "strom_batch_submit": (C.c_int, [P, P, P, PD, PD, C.POINTER(C.c_uint64)]),
     "strom_batch_step": (C.c_int, [P, C.c_int32, P, PI32, PI32]),
     "strom_batch_poll": (C.c_int, [P, C.c_uint64, C.POINTER(strom_result), C.POINTER(strom_certificate),
-                                   PD]),
+                                   PD, PD]),
     "strom_psd_plan_create": (C.c_int, [PI64, PI32, C.c_int32, C.c_int32, C.POINTER(P)]),
     "strom_psd_plan_destroy": (None, [P]),
     "strom_psd_execute": (C.c_int, [P, P, P, P, P]),

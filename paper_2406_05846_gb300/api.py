@@ -277,12 +277,12 @@ class Batch:
         check(lib().strom_batch_step(self.handle, iters, stream, C.byref(run), C.byref(q)), "strom_batch_step")
         return run.value, q.value
 
-    def poll(self, ticket: int):
-        """None while pending, else (Result, Certificate or None, latency_s)."""
-        r, c, lat = N.strom_result(), N.strom_certificate(), C.c_double()
+    def poll(self, ticket: int, with_service=False):
+        """None while pending, else (Result, Certificate or None, latency_s[, service_s])."""
+        r, c, lat, svc = N.strom_result(), N.strom_certificate(), C.c_double(), C.c_double()
         c.max_ratio = float("nan")
-        st = check(lib().strom_batch_poll(self.handle, ticket, C.byref(r), C.byref(c), C.byref(lat)),
-                   "strom_batch_poll")
+        st = check(lib().strom_batch_poll(self.handle, ticket, C.byref(r), C.byref(c), C.byref(lat),
+                                          C.byref(svc)), "strom_batch_poll")
         if st == N.STROM_PENDING:
             return None
         res = Result(r.status, r.iterations, r.pobj, r.dobj, r.eta_p, r.eta_d, r.eta_g, r.sigma, r.m_kept)
@@ -290,6 +290,8 @@ class Batch:
         if c.max_ratio == c.max_ratio:
             cert = Certificate(c.max_ratio, c.lower_bound, c.phat, c.xi, c.hmax, c.gmin, bool(c.feasible),
                                bool(c.rank_one), bool(c.certified), None, None)
+        if with_service:
+            return res, cert, lat.value, svc.value
         return res, cert, lat.value
 
 

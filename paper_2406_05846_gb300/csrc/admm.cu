@@ -138,6 +138,13 @@ __global__ void __launch_bounds__(1024) finalize_kernel(AdmmDev d, AdmmParams pr
       continue;
     }
     if (eta <= prm.tol) {
+      if (prm.precision == STROM_PREC_MIXED && d.inst_prec[i] == STROM_PREC_FP32) {
+        // mixed precision: an instance retires only on an iterate whose
+        // projection used the FP64 eigensolver (the final polish)
+        d.inst_prec[i] = STROM_PREC_FP64;
+        ++active_here;
+        continue;
+      }
       d.inst_active[i] = 0;
       d.inst_flag[i] = 1;
       continue;

@@ -81,6 +81,9 @@ struct PsdClasses {
   int max_n[4] = {0, 0, 0, 0};
 };
 
+// doubles of global scratch per FP64 block of the n <= 160 class (V^T, 160 x 162)
+constexpr size_t kVScratchPerBlock = 160 * 162;
+
 struct PsdArgs {
   const double* Xb;            // svec input
   double* out;                 // svec output

@@ -28,7 +28,7 @@ namespace strom {
 namespace {
 
 constexpr int FT = 256;       // threads per factorisation CTA
-constexpr int SOLVE_T = 128;  // threads per chain-solve CTA
+constexpr int SOLVE_T = 256;  // threads per chain-solve CTA
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -284,10 +284,26 @@ __global__ void __launch_bounds__(SOLVE_T) chain_solve_kernel(YsolveDev d, doubl
         }
       }
       __syncthreads();
-      for (int i = je + threadIdx.x; i < m; i += SOLVE_T) {
-        double acc = 0.0;
-        for (int jj = jb; jj < je; ++jj) acc += L[(int64_t)jj * m + i] * sh[jj];
-        sh[i] -= acc;
+      if (je - jb == 32) {
+        for (int i = je + threadIdx.x; i < m; i += SOLVE_T) {
+          const double* Li = L + (int64_t)jb * m + i;
+          double lv[32];
+#pragma unroll
+          for (int t = 0; t < 32; ++t) lv[t] = Li[(int64_t)t * m];  // 32 independent loads in flight
+          double acc0 = 0.0, acc1 = 0.0;
+#pragma unroll
+          for (int t = 0; t < 32; t += 2) {
+            acc0 += lv[t] * sh[jb + t];
+            acc1 += lv[t + 1] * sh[jb + t + 1];
+          }
+          sh[i] -= acc0 + acc1;
+        }
+      } else {
+        for (int i = je + threadIdx.x; i < m; i += SOLVE_T) {
+          double acc = 0.0;
+          for (int jj = jb; jj < je; ++jj) acc += L[(int64_t)jj * m + i] * sh[jj];
+          sh[i] -= acc;
+        }
       }
       __syncthreads();
     }

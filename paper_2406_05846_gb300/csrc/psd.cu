@@ -46,31 +46,45 @@ __device__ double block_sum(double v, double* red) {
   return s;
 }
 
+template <typename T> struct Vec;
+template <> struct Vec<float> { using type = float4; static constexpr int W = 4; };
+template <> struct Vec<double> { using type = double2; static constexpr int W = 2; };
+
 template <typename T, int NP, int NT, bool VSMEM>
 struct JacobiSmem {
-  static constexpr int LD = NP + 1;
-  static constexpr size_t a_bytes = sizeof(T) * NP * LD;
-  static constexpr size_t v_bytes = VSMEM ? sizeof(T) * NP * LD : 0;
-  static constexpr size_t rot_bytes = (sizeof(T) * 3 + sizeof(int) * 2) * (NP / 2);
+  static constexpr int LD = NP + 1;                  // A, row-major, odd stride
+  static constexpr int W = Vec<T>::W;
+  static constexpr int LDV = NP + W;                 // V^T rows, 16-byte aligned
+  static constexpr int H = NP / 2;
+  static constexpr size_t a_bytes = ((sizeof(T) * NP * LD + 15) / 16) * 16;
+  static constexpr size_t v_bytes = VSMEM ? sizeof(T) * NP * LDV : 0;
+  static constexpr size_t rot_bytes = (sizeof(T) * 3 + sizeof(int) * 2) * H;
   static constexpr size_t red_bytes = sizeof(double) * (NT / 32 + 2);
   static constexpr size_t total = a_bytes + v_bytes + rot_bytes + red_bytes + 64;
+  static constexpr int MAXA = (H * (H + 1) / 2 + NT - 1) / NT;     // 2x2 blocks (t1 <= t2) per thread
+  static constexpr int MAXV = (H * ((NP + W - 1) / W) + NT - 1) / NT;  // (pair, vector chunk) per thread
 };
 
+// One CTA diagonalises one block. A (full, symmetric) lives in shared memory;
+// the eigenvector matrix is kept transposed (row k = eigenvector k) so a
+// rotation of columns p, q of V is a rotation of two contiguous rows,
+// applied with 16-byte vector loads. Only the 2x2 blocks with t1 <= t2 are
+// computed; each one also writes its mirror image.
 template <typename T, int NP, int NT, bool VSMEM>
 __global__ void __launch_bounds__(NT) jacobi_psd_kernel(PsdArgs a, int list_start, double tol, int max_sweeps) {
   using SM = JacobiSmem<T, NP, NT, VSMEM>;
-  constexpr int LD = SM::LD;
+  using VT = typename Vec<T>::type;
+  constexpr int LD = SM::LD, LDV = SM::LDV, W = SM::W;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* A = reinterpret_cast<T*>(smem_raw);
   T* V = VSMEM ? reinterpret_cast<T*>(smem_raw + SM::a_bytes)
-               : reinterpret_cast<T*>(a.vscratch) + (size_t)blockIdx.x * NP * LD;
+               : reinterpret_cast<T*>(a.vscratch) + (size_t)blockIdx.x * NP * LDV;
   T* sT = reinterpret_cast<T*>(smem_raw + SM::a_bytes + SM::v_bytes);
-  T* sS = sT + NP / 2;
-  T* sU = sS + NP / 2;
-  int* sP = reinterpret_cast<int*>(sU + NP / 2);
-  int* sQ = sP + NP / 2;
+  T* sS = sT + SM::H;
+  T* sU = sS + SM::H;
+  int* sP = reinterpret_cast<int*>(sU + SM::H);
+  int* sQ = sP + SM::H;
   double* red = reinterpret_cast<double*>(smem_raw + SM::a_bytes + SM::v_bytes + SM::rot_bytes + 16);
-  // keep the reduction buffer 8-byte aligned
   red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(red) + 7) & ~uintptr_t(7));
 
   const int tid = threadIdx.x;
@@ -78,10 +92,11 @@ __global__ void __launch_bounds__(NT) jacobi_psd_kernel(PsdArgs a, int list_star
   if (a.blk_active != nullptr && a.blk_active[bid] == 0) return;
   const int n = a.blk_n[bid];
   const int np = n + (n & 1);
+  const int half = np / 2;
   const int64_t off = a.blk_off[bid];
   const double* __restrict__ xb = a.Xb + off;
 
-  // ---- unpack svec -> full symmetric matrix, V = I
+  // ---- unpack svec -> full symmetric matrix; V^T = I (padding included)
   double fro = 0.0;
   for (int idx = tid; idx < np * np; idx += NT) {
     const int i = idx % np, j = idx / np;
@@ -94,14 +109,37 @@ __global__ void __launch_bounds__(NT) jacobi_psd_kernel(PsdArgs a, int list_star
       fro += e * e;
     }
     A[i * LD + j] = v;
-    V[i * LD + j] = (i == j) ? T(1) : T(0);
+  }
+  for (int idx = tid; idx < np * LDV; idx += NT) {
+    const int k = idx / LDV, i = idx - (idx / LDV) * LDV;
+    V[idx] = (i == k) ? T(1) : T(0);
   }
   fro = block_sum<NT>(fro, red);   // contains a barrier
 
+  // ---- this thread's work items, fixed for all rounds
+  const int nAit = half * (half + 1) / 2;
+  const int nchunk = (np + W - 1) / W;
+  const int nVit = half * nchunk;
+  uint32_t itA[SM::MAXA], itV[SM::MAXV];
+#pragma unroll
+  for (int i = 0; i < SM::MAXA; ++i) {
+    const int idx = tid + i * NT;
+    uint32_t code = 0xffffffffu;
+    if (idx < nAit) {
+      int t1 = 0, base = 0;
+      while (base + (half - t1) <= idx) { base += half - t1; ++t1; }
+      const int t2 = t1 + (idx - base);
+      code = ((uint32_t)t1 << 16) | (uint32_t)t2;
+    }
+    itA[i] = code;
+  }
+#pragma unroll
+  for (int i = 0; i < SM::MAXV; ++i) {
+    const int idx = tid + i * NT;
+    itV[i] = (idx < nVit) ? (((uint32_t)(idx / nchunk) << 16) | (uint32_t)(idx % nchunk)) : 0xffffffffu;
+  }
+
   // ---- cyclic Jacobi sweeps, round-robin ordering
-  const int half = np / 2;
-  const int nA = half * half;
-  const int nV = np * half;
   const double thr = tol * tol * fro;
   for (int sweep = 0; sweep < max_sweeps && np > 1; ++sweep) {
     double off_sum = 0.0;
@@ -127,42 +165,57 @@ __global__ void __launch_bounds__(NT) jacobi_psd_kernel(PsdArgs a, int list_star
         sP[t] = p; sQ[t] = q; sT[t] = tt; sS[t] = s; sU[t] = ta;
       }
       __syncthreads();
-      for (int item = tid; item < nA + nV; item += NT) {
-        if (item < nA) {
-          const int t1 = item / half, t2 = item - (item / half) * half;
-          const int p1 = sP[t1], q1 = sQ[t1], p2 = sP[t2], q2 = sQ[t2];
-          const T x00 = A[p1 * LD + p2], x01 = A[p1 * LD + q2];
-          const T x10 = A[q1 * LD + p2], x11 = A[q1 * LD + q2];
-          T y00, y01, y10, y11;
-          if (t1 == t2) {
-            // annihilated pair: a_pp - t a_pq, a_qq + t a_pq, a_pq = 0
-            const T tt = sT[t1];
-            y00 = x00 - tt * x01;
-            y11 = x11 + tt * x01;
-            y01 = T(0);
-            y10 = T(0);
-          } else {
-            // J1^T X J2 written as corrections x - s (y + tau x) (Rutishauser):
-            // no rounding bias from c ~ 1 when the rotation is small
-            const T s1 = sS[t1], u1 = sU[t1], s2 = sS[t2], u2 = sU[t2];
-            const T r00 = x00 - s1 * (x10 + u1 * x00), r10 = x10 + s1 * (x00 - u1 * x10);
-            const T r01 = x01 - s1 * (x11 + u1 * x01), r11 = x11 + s1 * (x01 - u1 * x11);
-            y00 = r00 - s2 * (r01 + u2 * r00);
-            y01 = r01 + s2 * (r00 - u2 * r01);
-            y10 = r10 - s2 * (r11 + u2 * r10);
-            y11 = r11 + s2 * (r10 - u2 * r11);
-          }
+#pragma unroll
+      for (int i = 0; i < SM::MAXA; ++i) {
+        const uint32_t code = itA[i];
+        if (code == 0xffffffffu) continue;
+        const int t1 = (int)(code >> 16), t2 = (int)(code & 0xffffu);
+        const int p1 = sP[t1], q1 = sQ[t1], p2 = sP[t2], q2 = sQ[t2];
+        const T x00 = A[p1 * LD + p2], x01 = A[p1 * LD + q2];
+        const T x10 = A[q1 * LD + p2], x11 = A[q1 * LD + q2];
+        if (t1 == t2) {
+          // annihilated pair: a_pp - t a_pq, a_qq + t a_pq, a_pq = 0
+          const T tt = sT[t1];
+          A[p1 * LD + p1] = x00 - tt * x01;
+          A[q1 * LD + q1] = x11 + tt * x01;
+          A[p1 * LD + q1] = T(0);
+          A[q1 * LD + p1] = T(0);
+        } else {
+          // J1^T X J2 written as corrections x - s (y + tau x) (Rutishauser):
+          // no rounding bias from c ~ 1 when the rotation is small
+          const T s1 = sS[t1], u1 = sU[t1], s2 = sS[t2], u2 = sU[t2];
+          const T r00 = x00 - s1 * (x10 + u1 * x00), r10 = x10 + s1 * (x00 - u1 * x10);
+          const T r01 = x01 - s1 * (x11 + u1 * x01), r11 = x11 + s1 * (x01 - u1 * x11);
+          const T y00 = r00 - s2 * (r01 + u2 * r00);
+          const T y01 = r01 + s2 * (r00 - u2 * r01);
+          const T y10 = r10 - s2 * (r11 + u2 * r10);
+          const T y11 = r11 + s2 * (r10 - u2 * r11);
           A[p1 * LD + p2] = y00; A[p1 * LD + q2] = y01;
           A[q1 * LD + p2] = y10; A[q1 * LD + q2] = y11;
-        } else {
-          const int it = item - nA;
-          const int k = it / half, t = it - (it / half) * half;
-          const int p = sP[t], q = sQ[t];
-          const T s = sS[t], u = sU[t];
-          const T vp = V[k * LD + p], vq = V[k * LD + q];
-          V[k * LD + p] = vp - s * (vq + u * vp);
-          V[k * LD + q] = vq + s * (vp - u * vq);
+          A[p2 * LD + p1] = y00; A[q2 * LD + p1] = y01;
+          A[p2 * LD + q1] = y10; A[q2 * LD + q1] = y11;
         }
+      }
+#pragma unroll
+      for (int i = 0; i < SM::MAXV; ++i) {
+        const uint32_t code = itV[i];
+        if (code == 0xffffffffu) continue;
+        const int t = (int)(code >> 16), c = (int)(code & 0xffffu);
+        const int p = sP[t], q = sQ[t];
+        const T s = sS[t], u = sU[t];
+        VT* vp = reinterpret_cast<VT*>(V + p * LDV) + c;
+        VT* vq = reinterpret_cast<VT*>(V + q * LDV) + c;
+        VT a4 = *vp, b4 = *vq;
+        T* ae = reinterpret_cast<T*>(&a4);
+        T* be = reinterpret_cast<T*>(&b4);
+#pragma unroll
+        for (int e = 0; e < W; ++e) {
+          const T x = ae[e], y = be[e];
+          ae[e] = x - s * (y + u * x);
+          be[e] = y + s * (x - u * y);
+        }
+        *vp = a4;
+        *vq = b4;
       }
       __syncthreads();
     }
@@ -193,17 +246,17 @@ __global__ void __launch_bounds__(NT) jacobi_psd_kernel(PsdArgs a, int list_star
       }
       __syncthreads();
       const int kk = s_arg;
-      for (int i = tid; i < n; i += NT) a.topvec[lo + i] = (double)V[i * LD + kk];
+      for (int i = tid; i < n; i += NT) a.topvec[lo + i] = (double)V[kk * LDV + i];
     }
     __syncthreads();
   }
   if (a.out == nullptr) return;
 
-  // ---- recombination Pi = W W^T with W = V diag(sqrt(max(lam, 0)))
-  for (int idx = tid; idx < n * np; idx += NT) {
-    const int i = idx / np, k = idx - (idx / np) * np;
+  // ---- recombination Pi = W^T W with W = diag(sqrt(max(lam, 0))) V^T
+  for (int idx = tid; idx < np * LDV; idx += NT) {
+    const int k = idx / LDV;
     const T lk = (k < n) ? A[k * LD + k] : T(0);
-    V[i * LD + k] = (lk > T(0)) ? V[i * LD + k] * dsqrt_<T>(lk) : T(0);
+    V[idx] = (lk > T(0)) ? V[idx] * dsqrt_<T>(lk) : T(0);
   }
   __syncthreads();
   const int nt = n * (n + 1) / 2;
@@ -214,10 +267,8 @@ __global__ void __launch_bounds__(NT) jacobi_psd_kernel(PsdArgs a, int list_star
     while ((j + 1) * (j + 2) / 2 <= idx) ++j;
     while (j * (j + 1) / 2 > idx) --j;
     const int i = idx - j * (j + 1) / 2;
-    const T* wi = V + i * LD;
-    const T* wj = V + j * LD;
     T acc = T(0);
-    for (int k = 0; k < n; ++k) acc += wi[k] * wj[k];
+    for (int k = 0; k < n; ++k) acc += V[k * LDV + i] * V[k * LDV + j];
     double x = (double)acc;
     if (i != j) x *= 1.41421356237309504880;
     if (a.blk_inv_sigma != nullptr) x = (x - xb[idx]) * inv_sigma;
@@ -327,7 +378,7 @@ extern "C" int strom_psd_plan_create(const int64_t* blk_off, const int32_t* blk_
     p->n.upload(blk_n, nblk);
     p->list.upload(list.data(), list.size());
     p->lam_off.upload(lo.data(), nblk);
-    if (precision == STROM_PREC_FP64 && p->cls.count[3] > 0) p->vscratch.alloc((size_t)p->cls.count[3] * 160 * 161);
+    if (precision == STROM_PREC_FP64 && p->cls.count[3] > 0) p->vscratch.alloc((size_t)p->cls.count[3] * strom::kVScratchPerBlock);
     STROM_CUDA(cudaDeviceSynchronize());
     *out = p;
     return STROM_OK;

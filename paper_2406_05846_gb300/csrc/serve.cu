@@ -24,13 +24,15 @@ struct Request {
   bool has_prob = false;
   strom::Problem prob;
   double t_submit = 0.0;
+  double t_admit = 0.0;
 };
 
 struct Done {
   strom_result r{};
   strom_certificate c{};
   bool has_c = false;
-  double latency = 0.0;
+  double latency = 0.0;   // submit -> retirement
+  double service = 0.0;   // admission -> retirement
 };
 
 }  // namespace
@@ -92,6 +94,7 @@ void admit(strom_batch* B) {
     copy_h2d(s->norm_C.p + i, &nc, sizeof(double), st);
     STROM_CUDA(cudaStreamSynchronize(st));  // `at` and `nc` are stack data
     s->meta[i].b = rq.b;
+    rq.t_admit = now_s();
     B->slot_ticket[i] = (int64_t)rq.ticket;
     B->slot_req[i] = std::move(rq);
     adm.push_back(i);
@@ -148,6 +151,7 @@ void retire(strom_batch* B) {
       d.has_c = true;
     }
     d.latency = t - rq.t_submit;
+    d.service = t - rq.t_admit;
     B->done[rq.ticket] = d;
     B->slot_ticket[i] = -1;
   }
@@ -230,7 +234,7 @@ extern "C" int strom_batch_step(strom_batch* B, int32_t iters, void* stream, int
 }
 
 extern "C" int strom_batch_poll(strom_batch* B, uint64_t ticket, strom_result* r, strom_certificate* c,
-                                double* latency_s) {
+                                double* latency_s, double* service_s) {
   return guard([&]() -> int {
     if (!B) throw StatusError(STROM_ERR_INVALID, "strom_batch_poll: null batch");
     auto it = B->done.find(ticket);
@@ -241,6 +245,7 @@ extern "C" int strom_batch_poll(strom_batch* B, uint64_t ticket, strom_result* r
     if (r) *r = it->second.r;
     if (c && it->second.has_c) *c = it->second.c;
     if (latency_s) *latency_s = it->second.latency;
+    if (service_s) *service_s = it->second.service;
     return STROM_OK;
   });
 }

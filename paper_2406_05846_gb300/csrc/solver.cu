@@ -321,7 +321,7 @@ void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
   s->blk_act64.alloc(s->nblk);
   s->lam.alloc(std::max<int64_t>(1, lam_acc));
   s->topvec.alloc(std::max<int64_t>(1, lam_acc));
-  if (s->cls.count[3] > 0) s->vscratch.alloc((size_t)s->cls.count[3] * 160 * 161);
+  if (s->cls.count[3] > 0) s->vscratch.alloc((size_t)s->cls.count[3] * kVScratchPerBlock);
   // ---- device views
   YsolveDev& yd = s->yd;
   yd.rowptr = s->rowptr.p; yd.col = s->col.p; yd.val = s->val.p;
@@ -782,7 +782,7 @@ void strom::eig_instances(strom_solver* s, const std::vector<int>& inst, bool us
   DevBuf<int32_t> list;
   list.upload(ids.data(), ids.size(), s->stream);
   DevBuf<double> vs;
-  if (cls.count[3] > 0) vs.alloc((size_t)cls.count[3] * 160 * 161);
+  if (cls.count[3] > 0) vs.alloc((size_t)cls.count[3] * kVScratchPerBlock);
   PsdArgs a{};
   a.Xb = in;
   a.blk_off = s->blk_off.p;
@@ -833,7 +833,7 @@ void strom::solver_eig_blocks(strom_solver* s, int inst, bool use_Z, std::vector
   DevBuf<int32_t> list;
   list.upload(ids.data(), ids.size(), s->stream);
   DevBuf<double> vs;
-  if (cls.count[3] > 0) vs.alloc((size_t)cls.count[3] * 160 * 161);
+  if (cls.count[3] > 0) vs.alloc((size_t)cls.count[3] * kVScratchPerBlock);
   PsdArgs a{};
   a.Xb = in;
   a.out = nullptr;
