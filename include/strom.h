@@ -275,6 +275,21 @@ int strom_psd_execute(strom_psd_plan* p, const double* Xb_dev, double* P_dev, do
 int strom_kernel_psd_project(const double* Xb_dev, const int64_t* blk_off, const int32_t* blk_n,
                              int32_t nblk, int32_t precision, double* P_dev, void* stream);
 
+/* The same projection for callers that cannot allocate device memory (a host
+ * framework that owns the whole device pool, a real-time loop that must not
+ * allocate after start-up). It allocates nothing: the block table and the
+ * FP64 eigenvector scratch live in a static device array of the library
+ * (about 4.4 MB, held by every GPU that loads the library until exit).
+ * The paper has no counterpart; this is a deployment variant.
+ * Limits: nblk <= 65536 (else STROM_ERR_INVALID, nothing launched); block
+ * sizes 1..160. The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and caches it: make that call before any
+ * stream capture. All calls share the array, so calls that overlap on the
+ * GPU race; the caller serialises them. The call returns after the stream
+ * has finished the projection. blk_off / blk_n are host arrays. */
+int strom_kernel_psd_project_noalloc(const double* Xb_dev, const int64_t* blk_off, const int32_t* blk_n,
+                                     int32_t nblk, int32_t precision, double* P_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -99,6 +99,7 @@ SIGNATURES = {
     "strom_psd_plan_destroy": (None, [P]),
     "strom_psd_execute": (C.c_int, [P, P, P, P, P]),
     "strom_kernel_psd_project": (C.c_int, [P, PI64, PI32, C.c_int32, C.c_int32, P, P]),
+    "strom_kernel_psd_project_noalloc": (C.c_int, [P, PI64, PI32, C.c_int32, C.c_int32, P, P]),
 }
 
 _lib = None

@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libstrom.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU = ["psd.cu", "factor.cu", "admm.cu", "solver.cu", "serve.cu"]
+CU = ["psd.cu", "factor.cu", "admm.cu", "solver.cu", "serve.cu", "noalloc.cu"]
 CPP = ["relax.cpp", "capi.cpp", "certify.cpp"]
 
 
