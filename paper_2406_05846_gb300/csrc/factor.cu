@@ -134,6 +134,15 @@ __global__ void __launch_bounds__(FT) chain_factor_kernel(YsolveDev d, double ra
       }
       __syncthreads();
     }
+    // row-major copy of L_g for the backward substitution: lt[j * m + i] = L[j][i]
+    {
+      double* LT = d.lt + d.fac_off[g];
+      for (int64_t idx = threadIdx.x; idx < (int64_t)m * m; idx += FT) {
+        const int i = (int)(idx % m), j = (int)(idx / m);  // writes are coalesced in i
+        LT[(int64_t)j * m + i] = (i <= j) ? L[(int64_t)i * m + j] : 0.0;
+      }
+      __syncthreads();
+    }
     // inverses of the 32 x 32 diagonal blocks of L_g, with every dropped row j
     // replaced by e_j in L and by 0 in the inverse (so w_j = y_j = 0 there);
     // stored column-major per block: Dinv[t][j] at t * 32 + j.
@@ -263,25 +272,15 @@ __global__ void __launch_bounds__(SOLVE_T) chain_solve_kernel(YsolveDev d, doubl
     for (int jb = 0; jb < m; jb += 32) {
       const int je = min(jb + 32, m), bs = je - jb;
       const double* Db = Dg + (int64_t)(jb / 32) * 1024;
-      // w_b = Dinv_b t_b: warp w computes outputs j = w, w + nwarps, ...; lane t
-      // holds term t of the dot product (Dinv column-major: Dinv[t][j] at t*32+j)
+      // w_b = Dinv_b t_b, one thread per output (Dinv column-major: coalesced in j)
       {
-        const double tt = (lane < bs) ? sh[jb + lane] : 0.0;
-        double wv[32 / (SOLVE_T / 32)];
-#pragma unroll
-        for (int q = 0; q < 32 / (SOLVE_T / 32); ++q) {
-          const int j = warp + q * (SOLVE_T / 32);
-          const double v = (lane < bs) ? Db[lane * 32 + j] * tt : 0.0;
-          wv[q] = warp_sum(v);
+        double w = 0.0;
+        if (threadIdx.x < bs) {
+          const int j = threadIdx.x;
+          for (int t = 0; t < bs; ++t) w += Db[t * 32 + j] * sh[jb + t];
         }
         __syncthreads();
-        if (lane == 0) {
-#pragma unroll
-          for (int q = 0; q < 32 / (SOLVE_T / 32); ++q) {
-            const int j = warp + q * (SOLVE_T / 32);
-            if (j < bs) sh[jb + j] = wv[q];
-          }
-        }
+        if (threadIdx.x < bs) sh[jb + threadIdx.x] = w;
       }
       __syncthreads();
       if (je - jb == 32) {
@@ -326,36 +325,39 @@ __global__ void __launch_bounds__(SOLVE_T) chain_solve_kernel(YsolveDev d, doubl
     }
     __syncthreads();
     const int nb = (m + 31) / 32;
+    const double* LT = d.lt + d.fac_off[g];  // row-major copy: LT[j * m + i] = L[j][i]
     for (int b = nb - 1; b >= 0; --b) {
-      const int jb = b * 32, je = min(jb + 32, m);
-      // w_j -= sum_{i >= je} L[i][j] y_i for j in [jb, je)
-      for (int j = jb + warp; j < je; j += SOLVE_T / 32) {
-        const double* colj = L + (int64_t)j * m;
-        double s = 0.0;
-        for (int i = je + lane; i < m; i += 32) s += colj[i] * sh[i];
-        s = warp_sum(s);
-        if (lane == 0) sh[j] -= s;
+      const int jb = b * 32, je = min(jb + 32, m), bs = je - jb;
+      // y_b = Dinv_b^T w_b, one thread per output (no cross-lane reductions)
+      const double* Db = Dg + (int64_t)b * 1024;
+      double v = 0.0;
+      if (threadIdx.x < bs) {
+        const int j = threadIdx.x;
+        for (int t = 0; t < bs; ++t) v += Db[(int64_t)j * 32 + t] * sh[jb + t];
       }
       __syncthreads();
-      // y_b = Dinv_b^T w_b: output j is the dot of column j of Dinv with w_b
-      {
-        const double* Db = Dg + (int64_t)b * 1024;
-        const int bs = je - jb;
-        const double tt = (lane < bs) ? sh[jb + lane] : 0.0;
-        double wv[32 / (SOLVE_T / 32)];
+      if (threadIdx.x < bs) sh[jb + threadIdx.x] = v;
+      __syncthreads();
+      // upward update: w_i -= sum_{j in block} L[j][i] y_j for i < jb (coalesced in i)
+      if (bs == 32) {
+        for (int i = threadIdx.x; i < jb; i += SOLVE_T) {
+          const double* Li = LT + (int64_t)jb * m + i;
+          double lv[32];
 #pragma unroll
-        for (int q = 0; q < 32 / (SOLVE_T / 32); ++q) {
-          const int j = warp + q * (SOLVE_T / 32);
-          const double v = (lane < bs) ? Db[(int64_t)j * 32 + lane] * tt : 0.0;
-          wv[q] = warp_sum(v);
-        }
-        __syncthreads();
-        if (lane == 0) {
+          for (int t = 0; t < 32; ++t) lv[t] = Li[(int64_t)t * m];
+          double acc0 = 0.0, acc1 = 0.0;
 #pragma unroll
-          for (int q = 0; q < 32 / (SOLVE_T / 32); ++q) {
-            const int j = warp + q * (SOLVE_T / 32);
-            if (j < bs) sh[jb + j] = wv[q];
+          for (int t = 0; t < 32; t += 2) {
+            acc0 += lv[t] * sh[jb + t];
+            acc1 += lv[t + 1] * sh[jb + t + 1];
           }
+          sh[i] -= acc0 + acc1;
+        }
+      } else {
+        for (int i = threadIdx.x; i < jb; i += SOLVE_T) {
+          double acc = 0.0;
+          for (int jj = jb; jj < je; ++jj) acc += LT[(int64_t)jj * m + i] * sh[jj];
+          sh[i] -= acc;
         }
       }
       __syncthreads();

@@ -41,6 +41,7 @@ struct YsolveDev {
   const int32_t* coup_n;     // [ngroups] consensus rows of the previous group coupled to this one
   // factor storage
   double* fac;
+  double* lt;                // row-major copies of the L_g (same offsets as fac)
   const int64_t* fac_off;
   double* coup;
   const int64_t* coup_off;

@@ -293,6 +293,7 @@ void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
   s->inst_row_chunk.upload(rfirst.data(), rfirst.size(), st);
   s->norm_C.upload(normC.data(), normC.size(), st);
   s->fac.alloc(std::max<int64_t>(1, fac_off.back()));
+  s->lt.alloc(std::max<int64_t>(1, fac_off.back()));
   s->coup.alloc(std::max<int64_t>(1, coup_off.back()));
   s->diag0.alloc(std::max<size_t>(1, oth_rows.size()));
   s->keep.alloc(s->m);
@@ -334,7 +335,7 @@ void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
   yd.noth = (int64_t)oth_rows.size(); yd.oth_rows = s->oth_rows.p; yd.grp_beg = s->grp_beg.p; yd.grp_len = s->grp_len.p;
   yd.dropped = nullptr; yd.ndropped = 0;
   yd.inst_grp = s->inst_grp.p; yd.coup_n = s->coup_n.p;
-  yd.fac = s->fac.p; yd.fac_off = s->fac_off.p; yd.coup = s->coup.p; yd.coup_off = s->coup_off.p;
+  yd.fac = s->fac.p; yd.lt = s->lt.p; yd.fac_off = s->fac_off.p; yd.coup = s->coup.p; yd.coup_off = s->coup_off.p;
   yd.diag0 = s->diag0.p; yd.keep = s->keep.p; yd.keep_oth = s->keep_oth.p; yd.yo = s->yo.p; yd.inv_piv = s->inv_piv.p; yd.dinv = s->dinv.p; yd.dinv_off = s->dinv_off.p;
   yd.inst_active = nullptr;
   AdmmDev& ad = s->ad;

@@ -43,7 +43,7 @@ struct strom_solver {
   DevBuf<int64_t> rowptr, atptr, star_rep, star_row, oth_rows, grp_beg, fac_off, coup_off, blk_off, lam_off, dropped;
   DevBuf<int32_t> col, atrow, row_inst, star_ptr, star_inst, inst_grp, coup_n, grp_len, blk_n, blk_list, blk_inst;
   DevBuf<int32_t> inst_svec_chunk, inst_row_chunk, iters, n_active;
-  DevBuf<double> val, atval, b, C, omega, inv_rep_s, star_c, star_d, star_inv_s2, fac, coup, diag0;
+  DevBuf<double> val, atval, b, C, omega, inv_rep_s, star_c, star_d, star_inv_s2, fac, lt, coup, diag0;
   DevBuf<double> X, S, Xb, y, yh, r, rho, norm_b, norm_C, sigma, stats, part_svec, part_rows, blk_inv_sigma;
   DevBuf<double> vscratch, tmp_svec, lam, topvec, yo, inv_piv, dinv;
   DevBuf<int64_t> dinv_off;
