@@ -132,6 +132,9 @@ typedef struct {
                                 on an FP64 iterate with eta <= tol */
   int32_t check_every;       /* host checks for completion every this many iterations */
   double time_budget_s;      /* <= 0: none */
+  int32_t eig_warm_period;   /* FP32 eigensolver: start each block's sweeps from its eigenvectors of
+                                the previous iteration, restarting cold every this many iterations
+                                (0 = always cold); blocks of size <= 80 */
 } strom_options;
 
 void strom_options_default(strom_options* o);

@@ -96,6 +96,15 @@ struct PsdArgs {
   const int64_t* lam_off;
   double* topvec;              // optional eigenvector of the largest eigenvalue at lam_off[b]
   double* vscratch;            // FP64 V storage for the n <= 160 class: [count * 160 * 160]
+  // warm start of the FP32 eigensolver across ADMM iterations (nullable):
+  // the eigenvectors of block b are kept in vstore + vstore_off[b]; a block
+  // whose instance is at an iteration not divisible by warm_period starts its
+  // sweeps from B = V X_b V^T with those eigenvectors instead of from X_b
+  float* vstore;
+  const int64_t* vstore_off;
+  const int32_t* blk_inst;
+  const int32_t* inst_iter;
+  int warm_period;
 };
 
 // precision: STROM_PREC_FP64 or STROM_PREC_FP32

@@ -60,7 +60,10 @@ struct JacobiSmem {
   static constexpr size_t v_bytes = VSMEM ? sizeof(T) * NP * LDV : 0;
   static constexpr size_t rot_bytes = (sizeof(T) * 3 + sizeof(int) * 2) * H;
   static constexpr size_t red_bytes = sizeof(double) * (NT / 32 + 2);
-  static constexpr size_t total = a_bytes + v_bytes + rot_bytes + red_bytes + 64;
+  // T = A V^T of the warm start (FP32 classes with V in shared memory and NP <= 80)
+  static constexpr bool WARM = (sizeof(T) == 4) && VSMEM && (NP <= 80);
+  static constexpr size_t t_bytes = WARM ? ((sizeof(T) * NP * LD + 15) / 16) * 16 : 0;
+  static constexpr size_t total = a_bytes + v_bytes + rot_bytes + red_bytes + t_bytes + 64;
   static constexpr int MAXA = (H * (H + 1) / 2 + NT - 1) / NT;     // 2x2 blocks (t1 <= t2) per thread
   static constexpr int MAXV = (H * ((NP + W - 1) / W) + NT - 1) / NT;  // (pair, vector chunk) per thread
 };
@@ -86,6 +89,7 @@ __global__ void __launch_bounds__(NT) jacobi_psd_kernel(PsdArgs a, int list_star
   int* sQ = sP + SM::H;
   double* red = reinterpret_cast<double*>(smem_raw + SM::a_bytes + SM::v_bytes + SM::rot_bytes + 16);
   red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(red) + 7) & ~uintptr_t(7));
+  T* Tm = reinterpret_cast<T*>(smem_raw + ((SM::a_bytes + SM::v_bytes + SM::rot_bytes + SM::red_bytes + 16 + 15) / 16) * 16);
 
   const int tid = threadIdx.x;
   const int bid = a.blk_list[list_start + blockIdx.x];
@@ -93,6 +97,10 @@ __global__ void __launch_bounds__(NT) jacobi_psd_kernel(PsdArgs a, int list_star
   const int n = a.blk_n[bid];
   const int np = n + (n & 1);
   const int half = np / 2;
+  bool warm = false;
+  if constexpr (SM::WARM) {
+    if (a.vstore != nullptr) warm = (a.inst_iter[a.blk_inst[bid]] % a.warm_period) != 0;
+  }
   const int64_t off = a.blk_off[bid];
   const double* __restrict__ xb = a.Xb + off;
 
@@ -110,11 +118,59 @@ __global__ void __launch_bounds__(NT) jacobi_psd_kernel(PsdArgs a, int list_star
     }
     A[i * LD + j] = v;
   }
-  for (int idx = tid; idx < np * LDV; idx += NT) {
-    const int k = idx / LDV, i = idx - (idx / LDV) * LDV;
-    V[idx] = (i == k) ? T(1) : T(0);
+  if (warm) {
+    const float* vs = a.vstore + a.vstore_off[bid];
+    for (int idx = tid; idx < np * LDV; idx += NT) {
+      const int k = idx / LDV, i = idx - (idx / LDV) * LDV;
+      V[idx] = (i < np) ? (T)vs[k * np + i] : T(0);
+    }
+  } else {
+    for (int idx = tid; idx < np * LDV; idx += NT) {
+      const int k = idx / LDV, i = idx - (idx / LDV) * LDV;
+      V[idx] = (i == k) ? T(1) : T(0);
+    }
   }
   fro = block_sum<NT>(fro, red);   // contains a barrier
+  if constexpr (SM::WARM) {
+    if (warm) {
+      // B = V X V^T in the stored eigenbasis (V^T rows are the eigenvectors):
+      // Tm = A V^T, then A = V Tm, each thread a 2x2 tile
+      const int nt2 = (np / 2) * (np / 2);
+      for (int it = tid; it < nt2; it += NT) {
+        const int i0 = 2 * (it / (np / 2)), j0 = 2 * (it % (np / 2));
+        T c00 = 0, c01 = 0, c10 = 0, c11 = 0;
+        for (int k = 0; k < np; ++k) {
+          const T a0 = A[i0 * LD + k], a1 = A[(i0 + 1) * LD + k];
+          const T v0 = V[j0 * LDV + k], v1 = V[(j0 + 1) * LDV + k];
+          c00 += a0 * v0; c01 += a0 * v1; c10 += a1 * v0; c11 += a1 * v1;
+        }
+        Tm[i0 * LD + j0] = c00; Tm[i0 * LD + j0 + 1] = c01;
+        Tm[(i0 + 1) * LD + j0] = c10; Tm[(i0 + 1) * LD + j0 + 1] = c11;
+      }
+      __syncthreads();
+      for (int it = tid; it < nt2; it += NT) {
+        const int i0 = 2 * (it / (np / 2)), j0 = 2 * (it % (np / 2));
+        if (j0 < i0) continue;  // upper 2x2 tiles, mirrored below
+        T c00 = 0, c01 = 0, c10 = 0, c11 = 0;
+        for (int k = 0; k < np; ++k) {
+          const T v0 = V[i0 * LDV + k], v1 = V[(i0 + 1) * LDV + k];
+          const T t0 = Tm[k * LD + j0], t1 = Tm[k * LD + j0 + 1];
+          c00 += v0 * t0; c01 += v0 * t1; c10 += v1 * t0; c11 += v1 * t1;
+        }
+        if (i0 == j0) {
+          const T o = T(0.5) * (c01 + c10);
+          A[i0 * LD + i0] = c00; A[(i0 + 1) * LD + i0 + 1] = c11;
+          A[i0 * LD + i0 + 1] = o; A[(i0 + 1) * LD + i0] = o;
+        } else {
+          A[i0 * LD + j0] = c00; A[i0 * LD + j0 + 1] = c01;
+          A[(i0 + 1) * LD + j0] = c10; A[(i0 + 1) * LD + j0 + 1] = c11;
+          A[j0 * LD + i0] = c00; A[(j0 + 1) * LD + i0] = c01;
+          A[j0 * LD + i0 + 1] = c10; A[(j0 + 1) * LD + i0 + 1] = c11;
+        }
+      }
+      __syncthreads();
+    }
+  }
 
   // ---- this thread's work items, fixed for all rounds
   const int nAit = half * (half + 1) / 2;
@@ -221,6 +277,16 @@ __global__ void __launch_bounds__(NT) jacobi_psd_kernel(PsdArgs a, int list_star
     }
     off_sum = block_sum<NT>(off_sum, red);
     if (off_sum <= thr) break;
+  }
+
+  if constexpr (SM::WARM) {
+    if (a.vstore != nullptr) {
+      float* vs = a.vstore + a.vstore_off[bid];
+      for (int idx = tid; idx < np * np; idx += NT) {
+        const int k = idx / np, i = idx - (idx / np) * np;
+        vs[idx] = (float)V[k * LDV + i];
+      }
+    }
   }
 
   // ---- eigen outputs (ascending eigenvalues, top eigenvector)

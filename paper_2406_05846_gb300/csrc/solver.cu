@@ -56,8 +56,15 @@ void make_chunks(const std::vector<int64_t>& off, std::vector<Chunk>& ch, std::v
   first.back() = (int32_t)ch.size();
 }
 
-PsdArgs psd_args(strom_solver* s, const double* in, double* out, const uint8_t* act, bool admm) {
+PsdArgs psd_args(strom_solver* s, const double* in, double* out, const uint8_t* act, bool admm, bool warm = false) {
   PsdArgs a{};
+  if (warm && s->opt.eig_warm_period > 0) {
+    a.vstore = s->vstore.p;
+    a.vstore_off = s->vstore_off.p;
+    a.blk_inst = s->blk_inst.p;
+    a.inst_iter = s->iters.p;
+    a.warm_period = s->opt.eig_warm_period;
+  }
   a.Xb = in;
   a.out = out;
   a.blk_off = s->blk_off.p;
@@ -80,7 +87,7 @@ void enqueue_iteration(strom_solver* s, cudaStream_t st) {
   ysolve_apply(yd, s->ninst, s->max_group, s->r.p, s->yh.p, s->rho.p, st);
   // Step 2: X_b = X + sigma (A^* y - C), S = (Pi(X_b) - X_b) / sigma
   admm_xb(d, s->yh.p, s->Xb.p, st);
-  psd_launch(psd_args(s, s->Xb.p, s->S.p, s->blk_act32.p, true), s->cls, STROM_PREC_FP32, st);
+  psd_launch(psd_args(s, s->Xb.p, s->S.p, s->blk_act32.p, true, true), s->cls, STROM_PREC_FP32, st);
   psd_launch(psd_args(s, s->Xb.p, s->S.p, s->blk_act64.p, true), s->cls, STROM_PREC_FP64, st);
   // Step 3: r = b/sigma - A(X/sigma + S - C), y^{k+1} = (A A^*)^{-1} r
   admm_residual_rhs(d, s->S.p, s->r.p, st);
@@ -157,7 +164,8 @@ void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
   std::vector<int8_t> row_kind;
   std::vector<double> normC(count);
   s->inst_blk_off.assign(count + 1, 0);
-  int64_t lam_acc = 0, dinv_acc = 0;
+  int64_t lam_acc = 0, dinv_acc = 0, vstore_acc = 0;
+  std::vector<int64_t> vstore_off;
   for (int i = 0; i < count; ++i) {
     const Sdp& q = *sdps[i]->s;
     const int64_t so = s->svec_off[i], ro = s->row_off[i];
@@ -218,6 +226,9 @@ void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
       blk_inst.push_back(i);
       lam_off.push_back(lam_acc);
       lam_acc += q.block_n[k];
+      const int64_t npk = q.block_n[k] + (q.block_n[k] & 1);
+      vstore_off.push_back(vstore_acc);
+      vstore_acc += npk * npk;
     }
   }
   s->inst_blk_off[count] = (int64_t)blk_n.size();
@@ -287,6 +298,8 @@ void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
   s->blk_list.upload(list.data(), list.size(), st);
   s->blk_inst.upload(blk_inst.data(), blk_inst.size(), st);
   s->lam_off.upload(lam_off.data(), lam_off.size(), st);
+  s->vstore_off.upload(vstore_off.data(), vstore_off.size(), st);
+  s->vstore.alloc(std::max<int64_t>(1, vstore_acc));
   s->svec_chunks.upload(sch.data(), sch.size(), st);
   s->row_chunks.upload(rch.data(), rch.size(), st);
   s->inst_svec_chunk.upload(sfirst.data(), sfirst.size(), st);
@@ -381,6 +394,7 @@ extern "C" void strom_options_default(strom_options* o) {
   o->polish_eta = 1e-5;
   o->check_every = 50;
   o->time_budget_s = 0.0;
+  o->eig_warm_period = 20;
 }
 
 extern "C" int strom_solver_create(const strom_sdp* const* sdps, int32_t count, const strom_options* opt,
@@ -394,7 +408,7 @@ extern "C" int strom_solver_create(const strom_sdp* const* sdps, int32_t count, 
     else strom_options_default(&s->opt);
     const auto& o = s->opt;
     if (!(o.tol > 0) || o.maxiter < 1 || !(o.sigma0 > 0) || !(o.tau > 0 && o.tau < 2) || !(o.rank_tol > 0) ||
-        o.precision < 0 || o.precision > 2 || o.check_every < 1)
+        o.precision < 0 || o.precision > 2 || o.check_every < 1 || o.eig_warm_period < 0)
       throw StatusError(STROM_ERR_INVALID, "strom_solver_create: invalid options");
     STROM_CUDA(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
     solver_setup(s.get(), sdps, count);

@@ -74,3 +74,38 @@ def test_ysolve_matches_oracle(pend_batch):
         assert np.all(got[~red.keep] == 0.0)
         err = np.linalg.norm(got[red.keep] - want) / np.linalg.norm(want)
         assert err <= 1e-10, err
+
+
+_CART = {}
+
+
+def _cartpole_case():
+    """Cart-pole, horizon 2 (11-variable cliques: 78x78 moment and 12x12
+    localizing blocks), with its oracle row reduction computed once."""
+    if not _CART:
+        p = wl.cartpole_problem(N=2, x0=0.2, theta0=0.1)
+        o = OR.relax(p)
+        _CART["p"], _CART["red"] = p, OA.reduce(o)
+    return _CART["p"], _CART["red"]
+
+
+def test_cartpole_ysolve_and_iterations_match_oracle():
+    S = lib()
+    p, red = _cartpole_case()
+    solver = S.Solver([S.Problem(p).relax()], tol=1e-12, maxiter=25, check_every=1, precision=S.STROM_PREC_FP64)
+    assert np.array_equal(solver.kept_rows(0), red.keep)
+    # y-solve on a random right-hand side
+    rng = np.random.default_rng(4)
+    r = rng.standard_normal(solver.m_total)
+    rd = dev(r)
+    yd = torch.zeros_like(rd)
+    solver.kernel_solve(rd.data_ptr(), yd.data_ptr())
+    y = host(yd)
+    want = OA.YSolver(red.A)(r[red.keep])
+    assert np.linalg.norm(y[red.keep] - want) <= 1e-10 * np.linalg.norm(want)
+    # the first 25 iterations of Algorithm 1
+    solver.step(25)
+    X, Sg, _ = solver.state(0)
+    ref = OA.solve(red, OA.Options(tol=1e-12, maxiter=25))
+    assert np.linalg.norm(X - ref.X) <= 1e-9 * np.linalg.norm(ref.X)
+    assert np.linalg.norm(Sg - ref.S) <= 1e-9 * max(1.0, np.linalg.norm(ref.S))
