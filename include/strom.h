@@ -135,6 +135,10 @@ typedef struct {
   int32_t eig_warm_period;   /* FP32 eigensolver: start each block's sweeps from its eigenvectors of
                                 the previous iteration, restarting cold every this many iterations
                                 (0 = always cold); blocks of size <= 80 */
+  int32_t share_tail;        /* 1: when every instance has the same constraint rows after the first
+                                clique (e.g. one robot, different initial states), the factor of
+                                cliques 2..N is computed once and shared (cliques are eliminated
+                                N..1, so only the first clique's factor differs) */
 } strom_options;
 
 void strom_options_default(strom_options* o);

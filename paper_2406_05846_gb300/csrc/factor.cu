@@ -77,13 +77,19 @@ __global__ void __launch_bounds__(FT) assemble_kernel(YsolveDev d, const int32_t
 }
 
 // One CTA per instance: the chain factorisation, cliques N..1.
-__global__ void __launch_bounds__(FT) chain_factor_kernel(YsolveDev d, double rank_tol, const int32_t* __restrict__ ilist) {
+// zsave (nullable): store the Schur update E^T E that the first group receives
+// (shared with the instances that reuse this chain's later groups);
+// zuse (nullable, with first_only): apply that stored update instead of E^T E
+__global__ void __launch_bounds__(FT) chain_factor_kernel(YsolveDev d, double rank_tol, const int32_t* __restrict__ ilist,
+                                                          int first_only, double* zsave, const double* zuse) {
   const int inst = ilist ? ilist[blockIdx.x] : blockIdx.x;
   const int gbeg = d.inst_grp[inst], gend = d.inst_grp[inst + 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __shared__ double s_piv;
   __shared__ int s_keep;
-  for (int g = gend - 1; g >= gbeg; --g) {
+  // first_only: the groups after the first are shared with another instance
+  // and already factorised; only the first clique's group is done here
+  for (int g = first_only ? gbeg : gend - 1; g >= gbeg; --g) {
     const int64_t g0 = d.grp_beg[g];
     const int m = d.grp_len[g];
     double* L = d.fac + d.fac_off[g];
@@ -92,15 +98,24 @@ __global__ void __launch_bounds__(FT) chain_factor_kernel(YsolveDev d, double ra
       const int cn = d.coup_n[g + 1];
       const int nm = d.grp_len[g + 1];
       const double* E = d.coup + d.coup_off[g + 1];
+      const bool use_z = (zuse != nullptr) && first_only && g == gbeg;
       for (int pair = warp; pair < cn * cn; pair += FT / 32) {
         const int a = pair % cn, b = pair / cn;
         if (a < b) continue;
-        double s = 0.0;
-        for (int r = lane; r < nm; r += 32) s += E[(int64_t)a * nm + r] * E[(int64_t)b * nm + r];
-        s = warp_sum(s);
+        double sum = 0.0;
+        if (use_z) {
+          sum = (lane == 0) ? zuse[(int64_t)b * cn + a] : 0.0;
+        } else {
+          for (int r = lane; r < nm; r += 32) sum += E[(int64_t)a * nm + r] * E[(int64_t)b * nm + r];
+          sum = warp_sum(sum);
+        }
         if (lane == 0) {
           const int i = m - cn + a, j = m - cn + b;
-          L[(int64_t)j * m + i] -= s;
+          L[(int64_t)j * m + i] -= sum;
+          if (zsave != nullptr && g == gbeg) {
+            zsave[(int64_t)b * cn + a] = sum;
+            zsave[(int64_t)a * cn + b] = sum;
+          }
         }
       }
       __syncthreads();
@@ -396,12 +411,12 @@ __global__ void star_post_kernel(YsolveDev d, const double* __restrict__ r, doub
 }  // namespace
 
 void ysolve_factor(const YsolveDev& d, int ngroups, int ninst, double rank_tol, cudaStream_t st,
-                   const int32_t* glist, const int32_t* ilist) {
+                   const int32_t* glist, const int32_t* ilist, bool first_only, double* zsave, const double* zuse) {
   if (ngroups == 0 || ninst == 0) return;
   assemble_kernel<<<ngroups, FT, 0, st>>>(d, glist);
   STROM_CUDA(cudaGetLastError());
   count_launches(1);
-  chain_factor_kernel<<<ninst, FT, 0, st>>>(d, rank_tol, ilist);
+  chain_factor_kernel<<<ninst, FT, 0, st>>>(d, rank_tol, ilist, first_only ? 1 : 0, zsave, zuse);
   STROM_CUDA(cudaGetLastError());
   count_launches(1);
 }

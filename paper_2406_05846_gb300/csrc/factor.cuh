@@ -55,9 +55,14 @@ struct YsolveDev {
   const uint8_t* inst_active;  // nullable
 };
 
-// glist / ilist (device, nullable): factorise only these groups / instances
+// glist / ilist (device, nullable): factorise only these groups / instances;
+// first_only: only the first group of each listed instance (its later groups
+// are shared with an instance factorised before)
+// zsave / zuse: see chain_factor_kernel (the first group's Schur update, saved
+// by the instance that owns a shared chain and reused by the others)
 void ysolve_factor(const YsolveDev& d, int ngroups, int ninst, double rank_tol, cudaStream_t st,
-                   const int32_t* glist = nullptr, const int32_t* ilist = nullptr);
+                   const int32_t* glist = nullptr, const int32_t* ilist = nullptr, bool first_only = false,
+                   double* zsave = nullptr, const double* zuse = nullptr);
 void ysolve_apply(const YsolveDev& d, int ninst, int max_group, const double* r, double* y, double* rho,
                   cudaStream_t st);
 

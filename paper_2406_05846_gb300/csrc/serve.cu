@@ -44,6 +44,9 @@ struct strom_batch {
   std::vector<int64_t> rowptr;
   std::vector<int32_t> col;
   std::vector<int64_t> at_perm;   // A^T order -> CSR entry, inside one instance
+  std::vector<double> tmpl_val;   // template's A values (the shared factor of cliques 2..N comes from them)
+  std::vector<int32_t> row_clique;
+  std::vector<int8_t> row_kind;
   std::deque<Request> queue;
   std::vector<int64_t> slot_ticket;
   std::vector<Request> slot_req;
@@ -173,6 +176,9 @@ extern "C" int strom_batch_create(const strom_sdp* tmpl, int32_t slots, const st
     B->nnz = q.nnz();
     B->rowptr = q.rowptr;
     B->col = q.col;
+    B->tmpl_val = q.val;
+    B->row_clique = q.row_clique;
+    B->row_kind = q.row_kind;
     // A^T order of the entries of one instance (columns ascending, rows ascending)
     std::vector<int64_t> cnt(q.nsvec + 1, 0);
     for (int32_t c : q.col) cnt[c + 1]++;
@@ -199,6 +205,16 @@ extern "C" int strom_batch_submit(strom_batch* B, const strom_sdp* sdp, const st
     const Sdp& q = *sdp->s;
     if (q.nsvec != B->nsvec || q.m() != B->m || q.nnz() != B->nnz || q.rowptr != B->rowptr || q.col != B->col)
       throw StatusError(STROM_ERR_INVALID, "strom_batch_submit: SDP structure differs from the batch template");
+    if (B->s->shared_tail) {
+      for (int64_t r = 0; r < B->m; ++r) {
+        if (B->row_clique[r] == 0 && B->row_kind[r] != STROM_ROW_CONS) continue;
+        for (int64_t e = B->rowptr[r]; e < B->rowptr[r + 1]; ++e)
+          if (q.val[e] != B->tmpl_val[e])
+            throw StatusError(STROM_ERR_INVALID, "strom_batch_submit: the batch shares the factor of cliques 2..N and "
+                                                 "this request's constraints there differ from the template's "
+                                                 "(create the batch with share_tail = 0)");
+      }
+    }
     Request rq;
     rq.ticket = B->next++;
     rq.val = q.val;

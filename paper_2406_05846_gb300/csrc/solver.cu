@@ -140,8 +140,21 @@ void refactor(strom_solver* s) {
   std::vector<int> all(s->ninst);
   for (int i = 0; i < s->ninst; ++i) all[i] = i;
   s->m_kept.assign(s->ninst, 0);
-  factor_instances(s, all);
+  factor_instances(s, all, true);
   reset_state(s);
+}
+
+// true when b's constraint rows of cliques 2..N (and the consensus rows of
+// clique 1, which couple to clique 2) equal a's exactly, with the same layout
+bool same_tail(const Sdp& a, const Sdp& b) {
+  if (a.N != b.N || a.nv != b.nv || a.nsvec != b.nsvec || a.m() != b.m() || a.nnz() != b.nnz()) return false;
+  if (a.rowptr != b.rowptr || a.col != b.col || a.row_kind != b.row_kind || a.block_n != b.block_n) return false;
+  for (int64_t r = 0; r < a.m(); ++r) {
+    if (a.row_clique[r] == 0 && a.row_kind[r] != STROM_ROW_CONS) continue;
+    for (int64_t e = a.rowptr[r]; e < a.rowptr[r + 1]; ++e)
+      if (a.val[e] != b.val[e]) return false;
+  }
+  return true;
 }
 
 void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
@@ -155,16 +168,19 @@ void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
   }
   s->nsvec = s->svec_off[count];
   s->m = s->row_off[count];
+  s->shared_tail = (s->opt.share_tail != 0) && count > 1;
+  s->row_clique_h0 = sdps[0]->s->row_clique;
+  for (int i = 1; i < count && s->shared_tail; ++i) s->shared_tail = same_tail(*sdps[0]->s, *sdps[i]->s);
   if (s->nsvec > INT32_MAX || s->m > INT32_MAX) throw StatusError(STROM_ERR_INVALID, "batch too large for int32 indices");
   // ---- concatenated host arrays
-  std::vector<int64_t> dinv_off, rowptr(1, 0), star_rep, star_row, oth_rows, grp_beg, fac_off(1, 0), coup_off(1, 0), blk_off,
+  std::vector<int64_t> dinv_off, rowptr(1, 0), star_rep, star_row, oth_rows, grp_beg, fac_off, coup_off, blk_off,
       lam_off;
   std::vector<int32_t> col, row_inst, star_ptr, star_inst, inst_grp(1, 0), coup_n, blk_n, blk_inst;
   std::vector<double> val, b, C, omega, inv_rep_s, star_c, star_d, star_inv_s2;
   std::vector<int8_t> row_kind;
   std::vector<double> normC(count);
   s->inst_blk_off.assign(count + 1, 0);
-  int64_t lam_acc = 0, dinv_acc = 0, vstore_acc = 0;
+  int64_t lam_acc = 0, dinv_acc = 0, vstore_acc = 0, fac_acc = 0, coup_acc = 0;
   std::vector<int64_t> vstore_off;
   for (int i = 0; i < count; ++i) {
     const Sdp& q = *sdps[i]->s;
@@ -211,10 +227,19 @@ void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
       s->grp_full_cons.push_back(q.grp_cons[k]);
       const int cprev = (k > 0) ? q.grp_cons[k - 1] : 0;
       coup_n.push_back(cprev);
-      fac_off.push_back(fac_off.back() + mk * mk);
-      dinv_off.push_back(dinv_acc);
-      dinv_acc += ((mk + 31) / 32) * 1024;
-      coup_off.push_back(coup_off.back() + mk * cprev);
+      if (s->shared_tail && i > 0 && k > 0) {
+        // cliques 2..N share instance 0's factor storage
+        fac_off.push_back(fac_off[k]);
+        coup_off.push_back(coup_off[k]);
+        dinv_off.push_back(dinv_off[k]);
+      } else {
+        fac_off.push_back(fac_acc);
+        coup_off.push_back(coup_acc);
+        dinv_off.push_back(dinv_acc);
+        fac_acc += mk * mk;
+        coup_acc += mk * cprev;
+        dinv_acc += ((mk + 31) / 32) * 1024;
+      }
       s->max_group = std::max<int>(s->max_group, (int)mk);
     }
     inst_grp.push_back((int32_t)grp_beg.size());
@@ -305,9 +330,9 @@ void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
   s->inst_svec_chunk.upload(sfirst.data(), sfirst.size(), st);
   s->inst_row_chunk.upload(rfirst.data(), rfirst.size(), st);
   s->norm_C.upload(normC.data(), normC.size(), st);
-  s->fac.alloc(std::max<int64_t>(1, fac_off.back()));
-  s->lt.alloc(std::max<int64_t>(1, fac_off.back()));
-  s->coup.alloc(std::max<int64_t>(1, coup_off.back()));
+  s->fac.alloc(std::max<int64_t>(1, fac_acc));
+  s->lt.alloc(std::max<int64_t>(1, fac_acc));
+  s->coup.alloc(std::max<int64_t>(1, coup_acc));
   s->diag0.alloc(std::max<size_t>(1, oth_rows.size()));
   s->keep.alloc(s->m);
   s->keep_oth.alloc(std::max<size_t>(1, oth_rows.size()));
@@ -395,6 +420,7 @@ extern "C" void strom_options_default(strom_options* o) {
   o->check_every = 50;
   o->time_budget_s = 0.0;
   o->eig_warm_period = 20;
+  o->share_tail = 1;
 }
 
 extern "C" int strom_solver_create(const strom_sdp* const* sdps, int32_t count, const strom_options* opt,
@@ -488,33 +514,111 @@ static void upload_groups(strom_solver* s, const std::vector<int>& inst, const s
 // again on the kept rows only, so the triangular solves of every iteration
 // carry no dropped rows. Each group keeps its full-size storage, so one
 // instance can be refactorised without moving the others.
-void strom::factor_instances(strom_solver* s, const std::vector<int>& inst) {
+//
+// With a shared tail (every instance has instance 0's rows after the first
+// clique), instance 0 owns the factor of cliques 2..N; `tail` = true
+// (re)computes it. Every other instance factorises its first clique only,
+// reusing instance 0's coupling: in pass 1 through the saved Schur update of
+// the first group (all consensus rows), in pass 2 through instance 0's E.
+void strom::factor_instances(strom_solver* s, const std::vector<int>& inst, bool tail) {
   if (inst.empty()) return;
-  std::vector<int32_t> gl, il(inst.begin(), inst.end());
-  for (int i : inst)
-    for (int g = s->inst_grp_h[i]; g < s->inst_grp_h[i + 1]; ++g) gl.push_back(g);
-  DevBuf<int32_t> gd, id;
-  gd.upload(gl.data(), gl.size(), s->stream);
-  id.upload(il.data(), il.size(), s->stream);
-  // pass 1: full groups
-  for (int i : inst)
+  cudaStream_t st = s->stream;
+  const bool sh = s->shared_tail;
+  if (sh && tail && inst.size() > 1 && std::find(inst.begin(), inst.end(), 0) != inst.end()) {
+    // the other instances need instance 0's kept pattern and saved Schur
+    // update, so instance 0's two passes run to completion first
+    factor_instances(s, {0}, true);
+    std::vector<int> rest;
+    for (int i : inst)
+      if (i != 0) rest.push_back(i);
+    factor_instances(s, rest, false);
+    return;
+  }
+  std::vector<int> full, first;
+  for (int i : inst) {
+    if (sh && (i != 0 || !tail)) first.push_back(i);
+    else full.push_back(i);
+  }
+  if (sh && !first.empty() && s->tail_keep.empty() &&
+      std::find(full.begin(), full.end(), 0) == full.end())
+    throw StatusError(STROM_ERR_INVALID, "shared factor of cliques 2..N has not been computed");
+  auto run = [&](const std::vector<int>& which, bool first_only, double* zsave, const double* zuse) {
+    if (which.empty()) return;
+    std::vector<int32_t> gl, il(which.begin(), which.end());
+    for (int i : which) {
+      if (first_only) gl.push_back(s->inst_grp_h[i]);
+      else
+        for (int g = s->inst_grp_h[i]; g < s->inst_grp_h[i + 1]; ++g) gl.push_back(g);
+    }
+    DevBuf<int32_t> gd, id;
+    gd.upload(gl.data(), gl.size(), st);
+    id.upload(il.data(), il.size(), st);
+    ysolve_factor(s->yd, (int)gl.size(), (int)il.size(), s->opt.rank_tol, st, gd.p, id.p, first_only, zsave, zuse);
+    STROM_CUDA(cudaStreamSynchronize(st));
+  };
+  // local row of instance i whose keep flag instance 0 decided (rows after the first clique)
+  const int N0 = s->meta[0].N;
+  auto tail_row = [&](int i, int64_t local) -> bool {
+    (void)i;
+    return s->row_clique_h0[local] != 0;
+  };
+  (void)N0;
+  // tail groups of a first-only instance take instance 0's kept pattern
+  auto tail_lists = [&](int i, std::vector<int64_t>& oth, std::vector<int32_t>& kept_cons) {
+    for (int g = s->inst_grp_h[i] + 1; g < s->inst_grp_h[i + 1]; ++g) {
+      const int64_t b = s->grp_beg_h[g];
+      const int L = s->grp_full_len[g], C = s->grp_full_cons[g];
+      int len = 0, cons = 0;
+      for (int q = 0; q < L; ++q) {
+        const int64_t row = s->full_oth[b + q];
+        if (s->tail_keep[row - s->row_off[i]]) {
+          oth[b + len++] = row;
+          if (q >= L - C) ++cons;
+        }
+      }
+      for (int q = len; q < L; ++q) oth[b + q] = -1;
+      s->grp_len_h[g] = len;
+      kept_cons[g] = cons;
+    }
+  };
+  std::vector<int64_t> oth = s->full_oth;
+  std::vector<int32_t> kept_cons(s->ngroups, 0);
+  // ---- pass 1: all rows (first-only instances: their first clique's rows)
+  for (int i : full)
     for (int g = s->inst_grp_h[i]; g < s->inst_grp_h[i + 1]; ++g) {
       s->grp_len_h[g] = s->grp_full_len[g];
       s->coup_n_h[g] = (g > s->inst_grp_h[i]) ? s->grp_full_cons[g - 1] : 0;
     }
-  upload_groups(s, inst, s->full_oth);
-  for (int i : inst) {  // rows of these instances start as kept
-    const int64_t ro = s->row_off[i], m = s->row_off[i + 1] - ro;
-    STROM_CUDA(cudaMemsetAsync(s->keep.p + ro, 1, m, s->stream));
+  for (int i : first) {
+    const int g0 = s->inst_grp_h[i];
+    s->grp_len_h[g0] = s->grp_full_len[g0];
+    s->coup_n_h[g0] = 0;
+    tail_lists(i, oth, kept_cons);
+    if (g0 + 1 < s->inst_grp_h[i + 1]) s->coup_n_h[g0 + 1] = s->grp_full_cons[g0];  // all consensus rows, Z layout
+    for (int g = g0 + 2; g < s->inst_grp_h[i + 1]; ++g) s->coup_n_h[g] = kept_cons[g - 1];
   }
-  ysolve_factor(s->yd, (int)gl.size(), (int)il.size(), s->opt.rank_tol, s->stream, gd.p, id.p);
+  upload_groups(s, inst, oth);
   std::vector<uint8_t> keep(s->m);
-  copy_d2h(keep.data(), s->keep.p, s->m, s->stream);
-  STROM_CUDA(cudaStreamSynchronize(s->stream));
-  // pass 2: kept rows only
-  std::vector<int64_t> oth(s->full_oth.size(), -1);
-  std::vector<int32_t> kept_cons(s->ngroups, 0);
   for (int i : inst) {
+    const int64_t ro = s->row_off[i], m = s->row_off[i + 1] - ro;
+    for (int64_t r = 0; r < m; ++r) keep[ro + r] = 1;
+    if (std::find(first.begin(), first.end(), i) != first.end())
+      for (int64_t r = 0; r < m; ++r)
+        if (tail_row(i, r)) keep[ro + r] = s->tail_keep[r];
+    copy_h2d(s->keep.p + ro, keep.data() + ro, m, st);
+  }
+  if (sh && s->zshared.n == 0) s->zshared.alloc((size_t)s->grp_full_cons[0] * s->grp_full_cons[0] + 1);
+  run(full, false, sh ? s->zshared.p : nullptr, nullptr);
+  run(first, true, nullptr, s->zshared.p);
+  copy_d2h(keep.data(), s->keep.p, s->m, st);
+  STROM_CUDA(cudaStreamSynchronize(st));
+  if (sh && std::find(full.begin(), full.end(), 0) != full.end())
+    s->tail_keep.assign(keep.begin() + s->row_off[0], keep.begin() + s->row_off[1]);
+  // ---- pass 2: kept rows only
+  oth.assign(s->full_oth.size(), -1);
+  std::vector<int64_t> keep_oth_ones;
+  for (int i : inst) {
+    const bool fo = std::find(first.begin(), first.end(), i) != first.end();
     s->dropped_h[i].clear();
     for (int g = s->inst_grp_h[i]; g < s->inst_grp_h[i + 1]; ++g) {
       const int64_t b = s->grp_beg_h[g];
@@ -531,22 +635,45 @@ void strom::factor_instances(strom_solver* s, const std::vector<int>& inst) {
       }
       s->grp_len_h[g] = len;
       kept_cons[g] = cons;
+      if (fo && g > s->inst_grp_h[i])
+        for (int q = 0; q < len; ++q) keep_oth_ones.push_back(b + q);
     }
     for (int g = s->inst_grp_h[i]; g < s->inst_grp_h[i + 1]; ++g)
       s->coup_n_h[g] = (g > s->inst_grp_h[i]) ? kept_cons[g - 1] : 0;
+    if (fo) {
+      // the shared coupling has one column per consensus row instance 0 kept
+      const int g0 = s->inst_grp_h[i];
+      const int64_t r0 = s->row_off[i];
+      const int64_t b = s->grp_beg_h[g0];
+      const int L = s->grp_full_len[g0], C = s->grp_full_cons[g0];
+      for (int q = L - C; q < L; ++q) {
+        const int64_t row = s->full_oth[b + q];
+        if (keep[row] != s->tail_keep[row - r0])
+          throw StatusError(STROM_ERR_NOT_PD, "instance's consensus rows reduce differently from the shared "
+                                              "factor of cliques 2..N (use share_tail = 0)");
+      }
+    }
   }
   upload_groups(s, inst, oth);
-  ysolve_factor(s->yd, (int)gl.size(), (int)il.size(), s->opt.rank_tol, s->stream, gd.p, id.p);
+  if (!keep_oth_ones.empty()) {
+    std::vector<uint8_t> ko(s->full_oth.size(), 0);
+    copy_d2h(ko.data(), s->keep_oth.p, ko.size(), st);
+    STROM_CUDA(cudaStreamSynchronize(st));
+    for (int64_t q : keep_oth_ones) ko[q] = 1;
+    copy_h2d(s->keep_oth.p, ko.data(), ko.size(), st);
+  }
+  run(full, false, nullptr, nullptr);
+  run(first, true, nullptr, nullptr);
   // rows removed by the reduction, all instances
   std::vector<int64_t> dr;
   for (const auto& v : s->dropped_h) dr.insert(dr.end(), v.begin(), v.end());
-  s->dropped.upload(dr.data(), dr.size(), s->stream);
+  s->dropped.upload(dr.data(), dr.size(), st);
   s->yd.dropped = s->dropped.p;
   s->yd.ndropped = (int64_t)dr.size();
   // ||b_K|| and |K| of the refactorised instances
   std::vector<double> nb(s->ninst);
-  copy_d2h(nb.data(), s->norm_b.p, sizeof(double) * s->ninst, s->stream);
-  STROM_CUDA(cudaStreamSynchronize(s->stream));
+  copy_d2h(nb.data(), s->norm_b.p, sizeof(double) * s->ninst, st);
+  STROM_CUDA(cudaStreamSynchronize(st));
   for (int i : inst) {
     const auto& bv = s->meta[i].b;
     double acc = 0.0;
@@ -556,8 +683,8 @@ void strom::factor_instances(strom_solver* s, const std::vector<int>& inst) {
     nb[i] = std::sqrt(acc);
     s->m_kept[i] = kept;
   }
-  copy_h2d(s->norm_b.p, nb.data(), sizeof(double) * s->ninst, s->stream);
-  STROM_CUDA(cudaStreamSynchronize(s->stream));
+  copy_h2d(s->norm_b.p, nb.data(), sizeof(double) * s->ninst, st);
+  STROM_CUDA(cudaStreamSynchronize(st));
 }
 
 // X = S = y = 0, sigma = sigma0, active, iteration count 0, for a set of instances

@@ -39,6 +39,12 @@ struct strom_solver {
   std::vector<int32_t> grp_full_cons; // [ngroups] consensus rows closing each group
   std::vector<int32_t> grp_len_h, coup_n_h;      // current (compacted) lengths
   std::vector<std::vector<int64_t>> dropped_h;   // per instance
+  // shared tail: instance 0 owns the factor of its cliques 2..N and every
+  // other instance's groups after its first point to it
+  bool shared_tail = false;
+  std::vector<uint8_t> tail_keep;     // keep flags of instance 0's rows (local row order)
+  std::vector<int32_t> row_clique_h0; // clique of each row of instance 0
+  DevBuf<double> zshared;             // Schur update of instance 0's first group, all consensus rows
   // device data
   DevBuf<int64_t> rowptr, atptr, star_rep, star_row, oth_rows, grp_beg, fac_off, coup_off, blk_off, lam_off, dropped,
       vstore_off;
@@ -71,7 +77,7 @@ struct strom_solver {
 namespace strom {
 // solver internals used by the serving loop (solver.cu)
 void reset_instances(strom_solver* s, const std::vector<int>& inst);
-void factor_instances(strom_solver* s, const std::vector<int>& inst);
+void factor_instances(strom_solver* s, const std::vector<int>& inst, bool tail = false);
 void eig_instances(strom_solver* s, const std::vector<int>& inst, bool use_Z, std::vector<double>& lam,
                    std::vector<double>& topvec, std::vector<int64_t>& lam_off);
 int run_iterations(strom_solver* s, int iters, cudaStream_t user, int32_t* n_active);
