@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="strom", choices=["strom", "reference"])
-    ap.add_argument("--slots", type=int, default=512)
+    ap.add_argument("--slots", type=int, default=1024)
     ap.add_argument("--iters", type=int, default=800, help="sGS-ADMM iterations per step")
     ap.add_argument("--horizon", type=int, default=10)
     ap.add_argument("--maxiter", type=int, default=6000)
@@ -247,6 +247,9 @@ def run_strom(a, rank, world):
     svc = np.array([f[3] for f in ok]) if ok else np.array([np.nan])
     iters = np.array([f[0].iterations for f in ok]) if ok else np.array([0])
     cert_frac = float(np.mean([f[1].certified for f in ok])) if ok else 0.0
+    verdicts = {"rank_one": sum(f[1].rank_one for f in ok), "rollout_feasible": sum(f[1].feasible for f in ok),
+                "xi_le_1pct": sum(f[1].xi <= 1e-2 for f in ok), "certified": sum(f[1].certified for f in ok),
+                "of": len(ok)}
 
     # ---- end to end through the public API, continuing the same warmed batch:
     # each step builds its replacement requests from polynomial data
@@ -312,6 +315,7 @@ def run_strom(a, rank, world):
                           "plain_single_p50": float(np.median(plain_lat)) if plain_lat else None},
             "iterations": {"p50": float(np.percentile(iters, 50)), "p99": float(np.percentile(iters, 99))},
             "completed": len(finished), "counted": solved, "certified_fraction": cert_frac,
+            "rank1_certified_per_s": verdicts["certified"] / t, "verdicts": verdicts,
             "plain_fp64": plain, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
         }
         print(json.dumps(line))

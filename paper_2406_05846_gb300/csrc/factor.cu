@@ -275,11 +275,13 @@ __global__ void __launch_bounds__(SOLVE_T) chain_solve_kernel(YsolveDev d, doubl
       const int64_t ng0 = d.grp_beg[g + 1];
       const int nm = d.grp_len[g + 1];
       const double* E = d.coup + d.coup_off[g + 1];
+      // one warp per output, lanes over rows; the butterfly sum has a fixed
+      // order, the same in the multi-right-hand-side kernel
       for (int a = warp; a < cn; a += SOLVE_T / 32) {
-        double s = 0.0;
-        for (int rr = lane; rr < nm; rr += 32) s += E[(int64_t)a * nm + rr] * yo[ng0 + rr];
-        s = warp_sum(s);
-        if (lane == 0) sh[m - cn + a] -= s;
+        double acc = 0.0;
+        for (int rr = lane; rr < nm; rr += 32) acc += E[(int64_t)a * nm + rr] * yo[ng0 + rr];
+        acc = warp_sum(acc);
+        if (lane == 0) sh[m - cn + a] -= acc;
       }
       __syncthreads();
     }
@@ -304,13 +306,10 @@ __global__ void __launch_bounds__(SOLVE_T) chain_solve_kernel(YsolveDev d, doubl
           double lv[32];
 #pragma unroll
           for (int t = 0; t < 32; ++t) lv[t] = Li[(int64_t)t * m];  // 32 independent loads in flight
-          double acc0 = 0.0, acc1 = 0.0;
+          double acc = 0.0;  // one chain in t order: the same arithmetic as the multi-RHS kernel
 #pragma unroll
-          for (int t = 0; t < 32; t += 2) {
-            acc0 += lv[t] * sh[jb + t];
-            acc1 += lv[t + 1] * sh[jb + t + 1];
-          }
-          sh[i] -= acc0 + acc1;
+          for (int t = 0; t < 32; ++t) acc += lv[t] * sh[jb + t];
+          sh[i] -= acc;
         }
       } else {
         for (int i = je + threadIdx.x; i < m; i += SOLVE_T) {
@@ -360,13 +359,10 @@ __global__ void __launch_bounds__(SOLVE_T) chain_solve_kernel(YsolveDev d, doubl
           double lv[32];
 #pragma unroll
           for (int t = 0; t < 32; ++t) lv[t] = Li[(int64_t)t * m];
-          double acc0 = 0.0, acc1 = 0.0;
+          double acc = 0.0;
 #pragma unroll
-          for (int t = 0; t < 32; t += 2) {
-            acc0 += lv[t] * sh[jb + t];
-            acc1 += lv[t + 1] * sh[jb + t + 1];
-          }
-          sh[i] -= acc0 + acc1;
+          for (int t = 0; t < 32; ++t) acc += lv[t] * sh[jb + t];
+          sh[i] -= acc;
         }
       } else {
         for (int i = threadIdx.x; i < jb; i += SOLVE_T) {
@@ -380,6 +376,234 @@ __global__ void __launch_bounds__(SOLVE_T) chain_solve_kernel(YsolveDev d, doubl
     for (int i = threadIdx.x; i < m; i += SOLVE_T) {
       yo[g0 + i] = sh[i];
       y[d.oth_rows[g0 + i]] = sh[i];
+    }
+    __syncthreads();
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// Multi-right-hand-side chain solve for instances that share the factor of
+// cliques 2..N: one CTA serves a tile of R instances. For a shared group each
+// element of L (L^T, E, the 32x32 inverses) is loaded once and applied to the
+// R right-hand sides (columns) held in shared memory as sh[i * R + r], and
+// every barrier is paid once per R instances. The first clique's group has a
+// factor per instance and is done column by column.
+// ---------------------------------------------------------------------------
+
+// one column (stride R in sh) through a per-instance group, forward
+template <int R>
+__device__ void column_forward(const YsolveDev& d, int g, double* sh, int r, const double* __restrict__ yo,
+                               int ngrp_next) {
+  const int m = d.grp_len[g];
+  const double* L = d.fac + d.fac_off[g];
+  const double* Dg = d.dinv + d.dinv_off[g];
+  (void)ngrp_next;
+  for (int jb = 0; jb < m; jb += 32) {
+    const int je = min(jb + 32, m), bs = je - jb;
+    const double* Db = Dg + (int64_t)(jb / 32) * 1024;
+    double w = 0.0;
+    if (threadIdx.x < bs) {
+      const int j = threadIdx.x;
+      for (int t = 0; t < bs; ++t) w += Db[t * 32 + j] * sh[(jb + t) * R + r];
+    }
+    __syncthreads();
+    if (threadIdx.x < bs) sh[(jb + threadIdx.x) * R + r] = w;
+    __syncthreads();
+    for (int i = je + threadIdx.x; i < m; i += SOLVE_T) {
+      double acc = 0.0;
+      for (int jj = jb; jj < je; ++jj) acc += L[(int64_t)jj * m + i] * sh[jj * R + r];
+      sh[i * R + r] -= acc;
+    }
+    __syncthreads();
+  }
+}
+
+// one column (stride R in sh) through a per-instance group, backward
+template <int R>
+__device__ void column_backward(const YsolveDev& d, int g, double* sh, int r) {
+  const int m = d.grp_len[g];
+  const double* LT = d.lt + d.fac_off[g];
+  const double* Dg = d.dinv + d.dinv_off[g];
+  const int nb = (m + 31) / 32;
+  for (int b = nb - 1; b >= 0; --b) {
+    const int jb = b * 32, je = min(jb + 32, m), bs = je - jb;
+    const double* Db = Dg + (int64_t)b * 1024;
+    double v = 0.0;
+    if (threadIdx.x < bs) {
+      const int j = threadIdx.x;
+      for (int t = 0; t < bs; ++t) v += Db[(int64_t)j * 32 + t] * sh[(jb + t) * R + r];
+    }
+    __syncthreads();
+    if (threadIdx.x < bs) sh[(jb + threadIdx.x) * R + r] = v;
+    __syncthreads();
+    for (int i = threadIdx.x; i < jb; i += SOLVE_T) {
+      double acc = 0.0;
+      for (int jj = jb; jj < je; ++jj) acc += LT[(int64_t)jj * m + i] * sh[jj * R + r];
+      sh[i * R + r] -= acc;
+    }
+    __syncthreads();
+  }
+}
+
+template <int R>
+__global__ void __launch_bounds__(SOLVE_T) chain_solve_multi_kernel(YsolveDev d, int ninst, double* __restrict__ yo,
+                                                                   double* __restrict__ y) {
+  static_assert(32 * R <= SOLVE_T, "one thread per (output, column) of a 32x32 inverse product");
+  extern __shared__ double sh[];  // [max group size * R], element (i, r) at i * R + r
+  __shared__ int s_inst[R];
+  __shared__ int s_act[R];
+  const int i0 = blockIdx.x * R;
+  if (threadIdx.x < R) {
+    const int i = i0 + threadIdx.x;
+    const bool valid = i < ninst;
+    s_inst[threadIdx.x] = valid ? i : i0;  // columns past the end read instance i0 and are never written
+    s_act[threadIdx.x] = valid && (d.inst_active == nullptr || d.inst_active[i]);
+  }
+  __syncthreads();
+  int any = 0;
+#pragma unroll
+  for (int r = 0; r < R; ++r) any |= s_act[r];
+  if (!any) return;
+  const int NG = d.inst_grp[i0 + 1] - d.inst_grp[i0];
+  const int gl0 = d.inst_grp[i0];  // the tile's first instance: its shared-group offsets are everyone's
+
+  // ---- forward through the shared groups NG-1 .. 1
+  for (int k = NG - 1; k >= 1; --k) {
+    const int gl = gl0 + k;
+    const int m = d.grp_len[gl];
+    const double* L = d.fac + d.fac_off[gl];
+    const double* Dg = d.dinv + d.dinv_off[gl];
+    for (int idx = threadIdx.x; idx < m * R; idx += SOLVE_T) {
+      const int i = idx / R, r = idx - (idx / R) * R;
+      sh[idx] = yo[d.grp_beg[d.inst_grp[s_inst[r]] + k] + i];
+    }
+    __syncthreads();
+    if (k + 1 < NG) {
+      const int gn = gl + 1;
+      const int cn = d.coup_n[gn], nm = d.grp_len[gn];
+      const double* E = d.coup + d.coup_off[gn];
+      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      for (int idx = warp; idx < cn * R; idx += SOLVE_T / 32) {
+        const int a = idx / R, r = idx - (idx / R) * R;
+        const double* yn = yo + d.grp_beg[d.inst_grp[s_inst[r]] + k + 1];
+        double acc = 0.0;
+        for (int rr = lane; rr < nm; rr += 32) acc += E[(int64_t)a * nm + rr] * yn[rr];
+        acc = warp_sum(acc);
+        if (lane == 0) sh[(m - cn + a) * R + r] -= acc;
+      }
+      __syncthreads();
+    }
+    for (int jb = 0; jb < m; jb += 32) {
+      const int je = min(jb + 32, m), bs = je - jb;
+      const double* Db = Dg + (int64_t)(jb / 32) * 1024;
+      const int j = threadIdx.x / R, r = threadIdx.x - (threadIdx.x / R) * R;
+      double w = 0.0;
+      if (threadIdx.x < 32 * R && j < bs)
+        for (int t = 0; t < bs; ++t) w += Db[t * 32 + j] * sh[(jb + t) * R + r];
+      __syncthreads();
+      if (threadIdx.x < 32 * R && j < bs) sh[(jb + j) * R + r] = w;
+      __syncthreads();
+      for (int i = je + threadIdx.x; i < m; i += SOLVE_T) {
+        double acc[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) acc[q] = 0.0;
+        for (int t = 0; t < bs; ++t) {
+          const double l = L[(int64_t)(jb + t) * m + i];
+#pragma unroll
+          for (int q = 0; q < R; ++q) acc[q] += l * sh[(jb + t) * R + q];
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) sh[i * R + q] -= acc[q];
+      }
+      __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < m * R; idx += SOLVE_T) {
+      const int i = idx / R, r = idx - (idx / R) * R;
+      if (s_act[r]) yo[d.grp_beg[d.inst_grp[s_inst[r]] + k] + i] = sh[idx];
+    }
+    __syncthreads();
+  }
+
+  // ---- the first clique's group, per column (its factor is per instance)
+  for (int r = 0; r < R; ++r) {
+    if (!s_act[r]) continue;
+    const int g = d.inst_grp[s_inst[r]];
+    const int m = d.grp_len[g];
+    const int64_t g0 = d.grp_beg[g];
+    for (int i = threadIdx.x; i < m; i += SOLVE_T) sh[i * R + r] = yo[g0 + i];
+    __syncthreads();
+    if (NG > 1) {  // coupling with the shared group 2 (its w is in yo)
+      const int cn = d.coup_n[g + 1], nm = d.grp_len[g + 1];
+      const double* E = d.coup + d.coup_off[g + 1];
+      const double* yn = yo + d.grp_beg[g + 1];
+      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      for (int a = warp; a < cn; a += SOLVE_T / 32) {
+        double acc = 0.0;
+        for (int rr = lane; rr < nm; rr += 32) acc += E[(int64_t)a * nm + rr] * yn[rr];
+        acc = warp_sum(acc);
+        if (lane == 0) sh[(m - cn + a) * R + r] -= acc;
+      }
+      __syncthreads();
+    }
+    column_forward<R>(d, g, sh, r, yo, 0);
+    // backward for this group right away: it has no previous group
+    column_backward<R>(d, g, sh, r);
+    for (int i = threadIdx.x; i < m; i += SOLVE_T) {
+      yo[g0 + i] = sh[i * R + r];
+      y[d.oth_rows[g0 + i]] = sh[i * R + r];
+    }
+    __syncthreads();
+  }
+
+  // ---- backward through the shared groups 1 .. NG-1
+  for (int k = 1; k < NG; ++k) {
+    const int gl = gl0 + k;
+    const int m = d.grp_len[gl];
+    const double* LT = d.lt + d.fac_off[gl];
+    const double* Dg = d.dinv + d.dinv_off[gl];
+    const int cprev = d.coup_n[gl];
+    const double* E = d.coup + d.coup_off[gl];
+    for (int idx = threadIdx.x; idx < m * R; idx += SOLVE_T) {
+      const int i = idx / R, r = idx - (idx / R) * R;
+      const int gr = d.inst_grp[s_inst[r]] + k;
+      const int64_t pc = d.grp_beg[gr - 1] + d.grp_len[gr - 1] - cprev;
+      double w = yo[d.grp_beg[gr] + i];
+      for (int c = 0; c < cprev; ++c) w -= E[(int64_t)c * m + i] * yo[pc + c];
+      sh[idx] = w;
+    }
+    __syncthreads();
+    const int nb = (m + 31) / 32;
+    for (int b = nb - 1; b >= 0; --b) {
+      const int jb = b * 32, je = min(jb + 32, m), bs = je - jb;
+      const double* Db = Dg + (int64_t)b * 1024;
+      const int j = threadIdx.x / R, r = threadIdx.x - (threadIdx.x / R) * R;
+      double v = 0.0;
+      if (threadIdx.x < 32 * R && j < bs)
+        for (int t = 0; t < bs; ++t) v += Db[(int64_t)j * 32 + t] * sh[(jb + t) * R + r];
+      __syncthreads();
+      if (threadIdx.x < 32 * R && j < bs) sh[(jb + j) * R + r] = v;
+      __syncthreads();
+      for (int i = threadIdx.x; i < jb; i += SOLVE_T) {
+        double acc[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) acc[q] = 0.0;
+        for (int t = 0; t < bs; ++t) {
+          const double l = LT[(int64_t)(jb + t) * m + i];
+#pragma unroll
+          for (int q = 0; q < R; ++q) acc[q] += l * sh[(jb + t) * R + q];
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) sh[i * R + q] -= acc[q];
+      }
+      __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < m * R; idx += SOLVE_T) {
+      const int i = idx / R, r = idx - (idx / R) * R;
+      if (!s_act[r]) continue;
+      const int64_t gb = d.grp_beg[d.inst_grp[s_inst[r]] + k];
+      yo[gb + i] = sh[idx];
+      y[d.oth_rows[gb + i]] = sh[idx];
     }
     __syncthreads();
   }
@@ -410,6 +634,16 @@ __global__ void star_post_kernel(YsolveDev d, const double* __restrict__ r, doub
 
 }  // namespace
 
+void ysolve_configure(int max_group) {
+  const int bytes = (int)(sizeof(double) * (size_t)max_group * 8);
+  if (bytes > 48 * 1024) {
+    STROM_CUDA(cudaFuncSetAttribute(chain_solve_multi_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    STROM_CUDA(cudaFuncSetAttribute(chain_solve_multi_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes / 2));
+    STROM_CUDA(cudaFuncSetAttribute(chain_solve_multi_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes / 4));
+    STROM_CUDA(cudaFuncSetAttribute(chain_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes / 8));
+  }
+}
+
 void ysolve_factor(const YsolveDev& d, int ngroups, int ninst, double rank_tol, cudaStream_t st,
                    const int32_t* glist, const int32_t* ilist, bool first_only, double* zsave, const double* zuse) {
   if (ngroups == 0 || ninst == 0) return;
@@ -436,7 +670,15 @@ void ysolve_apply(const YsolveDev& d, int ninst, int max_group, const double* r,
   other_rhs_kernel<<<ceil_div(d.noth, 256), 256, 0, st>>>(d, r, rho, d.yo);
   STROM_CUDA(cudaGetLastError());
   count_launches(1);
-  chain_solve_kernel<<<ninst, SOLVE_T, sizeof(double) * max_group, st>>>(d, d.yo, y);
+  if (d.tile_r > 1) {
+    const size_t smem = sizeof(double) * (size_t)max_group * d.tile_r;
+    const int grid = (ninst + d.tile_r - 1) / d.tile_r;
+    if (d.tile_r == 2) chain_solve_multi_kernel<2><<<grid, SOLVE_T, smem, st>>>(d, ninst, d.yo, y);
+    else if (d.tile_r == 4) chain_solve_multi_kernel<4><<<grid, SOLVE_T, smem, st>>>(d, ninst, d.yo, y);
+    else chain_solve_multi_kernel<8><<<grid, SOLVE_T, smem, st>>>(d, ninst, d.yo, y);
+  } else {
+    chain_solve_kernel<<<ninst, SOLVE_T, sizeof(double) * max_group, st>>>(d, d.yo, y);
+  }
   STROM_CUDA(cudaGetLastError());
   count_launches(1);
   if (d.nclass > 0) {

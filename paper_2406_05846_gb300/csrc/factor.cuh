@@ -53,6 +53,7 @@ struct YsolveDev {
   double* dinv;              // inverses of the 32 x 32 diagonal blocks of every L_g
   const int64_t* dinv_off;   // [ngroups]
   const uint8_t* inst_active;  // nullable
+  int tile_r;                // > 1: multi-right-hand-side solve over tiles of this many instances (shared tail)
 };
 
 // glist / ilist (device, nullable): factorise only these groups / instances;
@@ -63,6 +64,8 @@ struct YsolveDev {
 void ysolve_factor(const YsolveDev& d, int ngroups, int ninst, double rank_tol, cudaStream_t st,
                    const int32_t* glist = nullptr, const int32_t* ilist = nullptr, bool first_only = false,
                    double* zsave = nullptr, const double* zuse = nullptr);
+// dynamic shared memory limits of the chain solves for groups up to max_group rows
+void ysolve_configure(int max_group);
 void ysolve_apply(const YsolveDev& d, int ninst, int max_group, const double* r, double* y, double* rho,
                   cudaStream_t st);
 

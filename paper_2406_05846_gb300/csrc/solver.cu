@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <vector>
@@ -376,6 +377,18 @@ void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
   yd.fac = s->fac.p; yd.lt = s->lt.p; yd.fac_off = s->fac_off.p; yd.coup = s->coup.p; yd.coup_off = s->coup_off.p;
   yd.diag0 = s->diag0.p; yd.keep = s->keep.p; yd.keep_oth = s->keep_oth.p; yd.yo = s->yo.p; yd.inv_piv = s->inv_piv.p; yd.dinv = s->dinv.p; yd.dinv_off = s->dinv_off.p;
   yd.inst_active = nullptr;
+  // tiles of the multi-right-hand-side solve (shared tail only): enough tiles
+  // to keep every SM busy; STROM_TILE_R overrides (1, 2, 4 or 8)
+  yd.tile_r = 1;
+  if (s->shared_tail) {
+    const int sms = 152;
+    yd.tile_r = count >= 2 * sms ? 2 : 1;  // measured best for the pendulum (L2-resident shared part)
+    if (const char* e = std::getenv("STROM_TILE_R")) {
+      const int v = std::atoi(e);
+      if (v == 1 || v == 2 || v == 4 || v == 8) yd.tile_r = v;
+    }
+  }
+  ysolve_configure(s->max_group);
   AdmmDev& ad = s->ad;
   ad.ninst = count; ad.nblk = s->nblk;
   ad.n_svec_chunks = (int)sch.size(); ad.n_row_chunks = (int)rch.size();
