@@ -129,6 +129,9 @@ __global__ void __launch_bounds__(1024) finalize_kernel(AdmmDev d, AdmmParams pr
     const double eg = fabs(cx - by) / (1.0 + fabs(cx) + fabs(by));
     const int it = d.iters[i] + 1;
     d.iters[i] = it;
+    // this iteration's projection used the FP64 eigensolver iff the instance
+    // was in FP64 mode before the switches below
+    d.iters64[i] = (d.inst_prec[i] == STROM_PREC_FP64) ? d.iters64[i] + 1 : 0;
     double* st = d.stats + 8 * (int64_t)i;
     st[0] = ep; st[1] = ed; st[2] = eg; st[3] = cx; st[4] = by;
     const double eta = fmax(ep, fmax(ed, eg));

@@ -38,6 +38,7 @@ struct AdmmDev {
   uint8_t* inst_flag;   // 0 running, 1 converged, 2 numerical, 3 maxiter
   uint8_t* inst_prec;
   int32_t* iters;
+  int32_t* iters64;     // consecutive iterations projected with the FP64 eigensolver
   double* stats;        // [ninst * 8]: eta_p, eta_d, eta_g, pobj, dobj
   double* part_svec;
   double* part_rows;

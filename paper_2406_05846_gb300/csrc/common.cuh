@@ -105,6 +105,10 @@ struct PsdArgs {
   const int32_t* blk_inst;
   const int32_t* inst_iter;
   int warm_period;
+  // the same for the FP64 eigensolver (the polish): eigenvectors in vstore64,
+  // inst_iter64 counts an instance's consecutive FP64 iterations
+  double* vstore64;
+  const int32_t* inst_iter64;
 };
 
 // precision: STROM_PREC_FP64 or STROM_PREC_FP32

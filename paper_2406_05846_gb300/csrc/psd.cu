@@ -61,7 +61,7 @@ struct JacobiSmem {
   static constexpr size_t rot_bytes = (sizeof(T) * 3 + sizeof(int) * 2) * H;
   static constexpr size_t red_bytes = sizeof(double) * (NT / 32 + 2);
   // T = A V^T of the warm start (FP32 classes with V in shared memory and NP <= 80)
-  static constexpr bool WARM = (sizeof(T) == 4) && VSMEM && (NP <= 80);
+  static constexpr bool WARM = VSMEM && (NP <= 80);
   static constexpr size_t t_bytes = WARM ? ((sizeof(T) * NP * LD + 15) / 16) * 16 : 0;
   static constexpr size_t total = a_bytes + v_bytes + rot_bytes + red_bytes + t_bytes + 64;
   static constexpr int MAXA = (H * (H + 1) / 2 + NT - 1) / NT;     // 2x2 blocks (t1 <= t2) per thread
@@ -97,9 +97,12 @@ __global__ void __launch_bounds__(NT) jacobi_psd_kernel(PsdArgs a, int list_star
   const int n = a.blk_n[bid];
   const int np = n + (n & 1);
   const int half = np / 2;
+  // warm start: the eigenvectors of this block from the instance's previous
+  // iteration in the same precision (FP32 store / FP64 store)
   bool warm = false;
   if constexpr (SM::WARM) {
-    if (a.vstore != nullptr) warm = (a.inst_iter[a.blk_inst[bid]] % a.warm_period) != 0;
+    if (sizeof(T) == 4 && a.vstore != nullptr) warm = (a.inst_iter[a.blk_inst[bid]] % a.warm_period) != 0;
+    if (sizeof(T) == 8 && a.vstore64 != nullptr) warm = (a.inst_iter64[a.blk_inst[bid]] % a.warm_period) != 0;
   }
   const int64_t off = a.blk_off[bid];
   const double* __restrict__ xb = a.Xb + off;
@@ -119,10 +122,18 @@ __global__ void __launch_bounds__(NT) jacobi_psd_kernel(PsdArgs a, int list_star
     A[i * LD + j] = v;
   }
   if (warm) {
-    const float* vs = a.vstore + a.vstore_off[bid];
-    for (int idx = tid; idx < np * LDV; idx += NT) {
-      const int k = idx / LDV, i = idx - (idx / LDV) * LDV;
-      V[idx] = (i < np) ? (T)vs[k * np + i] : T(0);
+    if constexpr (sizeof(T) == 4) {
+      const float* vs = a.vstore + a.vstore_off[bid];
+      for (int idx = tid; idx < np * LDV; idx += NT) {
+        const int k = idx / LDV, i = idx - (idx / LDV) * LDV;
+        V[idx] = (i < np) ? (T)vs[k * np + i] : T(0);
+      }
+    } else {
+      const double* vs = a.vstore64 + a.vstore_off[bid];
+      for (int idx = tid; idx < np * LDV; idx += NT) {
+        const int k = idx / LDV, i = idx - (idx / LDV) * LDV;
+        V[idx] = (i < np) ? (T)vs[k * np + i] : T(0);
+      }
     }
   } else {
     for (int idx = tid; idx < np * LDV; idx += NT) {
@@ -280,11 +291,18 @@ __global__ void __launch_bounds__(NT) jacobi_psd_kernel(PsdArgs a, int list_star
   }
 
   if constexpr (SM::WARM) {
-    if (a.vstore != nullptr) {
+    if (sizeof(T) == 4 && a.vstore != nullptr) {
       float* vs = a.vstore + a.vstore_off[bid];
       for (int idx = tid; idx < np * np; idx += NT) {
         const int k = idx / np, i = idx - (idx / np) * np;
         vs[idx] = (float)V[k * LDV + i];
+      }
+    }
+    if (sizeof(T) == 8 && a.vstore64 != nullptr) {
+      double* vs = a.vstore64 + a.vstore_off[bid];
+      for (int idx = tid; idx < np * np; idx += NT) {
+        const int k = idx / np, i = idx - (idx / np) * np;
+        vs[idx] = (double)V[k * LDV + i];
       }
     }
   }

@@ -57,13 +57,16 @@ void make_chunks(const std::vector<int64_t>& off, std::vector<Chunk>& ch, std::v
   first.back() = (int32_t)ch.size();
 }
 
-PsdArgs psd_args(strom_solver* s, const double* in, double* out, const uint8_t* act, bool admm, bool warm = false) {
+PsdArgs psd_args(strom_solver* s, const double* in, double* out, const uint8_t* act, bool admm, bool warm = false,
+                 bool warm64 = false) {
   PsdArgs a{};
-  if (warm && s->opt.eig_warm_period > 0) {
-    a.vstore = s->vstore.p;
+  if ((warm || warm64) && s->opt.eig_warm_period > 0) {
+    a.vstore = warm ? s->vstore.p : nullptr;
+    a.vstore64 = warm64 ? s->vstore64.p : nullptr;
     a.vstore_off = s->vstore_off.p;
     a.blk_inst = s->blk_inst.p;
     a.inst_iter = s->iters.p;
+    a.inst_iter64 = s->iters64.p;
     a.warm_period = s->opt.eig_warm_period;
   }
   a.Xb = in;
@@ -89,7 +92,7 @@ void enqueue_iteration(strom_solver* s, cudaStream_t st) {
   // Step 2: X_b = X + sigma (A^* y - C), S = (Pi(X_b) - X_b) / sigma
   admm_xb(d, s->yh.p, s->Xb.p, st);
   psd_launch(psd_args(s, s->Xb.p, s->S.p, s->blk_act32.p, true, true), s->cls, STROM_PREC_FP32, st);
-  psd_launch(psd_args(s, s->Xb.p, s->S.p, s->blk_act64.p, true), s->cls, STROM_PREC_FP64, st);
+  psd_launch(psd_args(s, s->Xb.p, s->S.p, s->blk_act64.p, true, false, true), s->cls, STROM_PREC_FP64, st);
   // Step 3: r = b/sigma - A(X/sigma + S - C), y^{k+1} = (A A^*)^{-1} r
   admm_residual_rhs(d, s->S.p, s->r.p, st);
   ysolve_apply(yd, s->ninst, s->max_group, s->r.p, s->y.p, s->rho.p, st);
@@ -124,6 +127,7 @@ void reset_state(strom_solver* s) {
   s->y.zero(s->stream);
   s->yh.zero(s->stream);
   s->iters.zero(s->stream);
+  s->iters64.zero(s->stream);
   s->inst_flag.zero(s->stream);
   s->stats.zero(s->stream);
   std::vector<double> sg(s->ninst, s->opt.sigma0);
@@ -326,6 +330,7 @@ void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
   s->lam_off.upload(lam_off.data(), lam_off.size(), st);
   s->vstore_off.upload(vstore_off.data(), vstore_off.size(), st);
   s->vstore.alloc(std::max<int64_t>(1, vstore_acc));
+  s->vstore64.alloc(std::max<int64_t>(1, vstore_acc));
   s->svec_chunks.upload(sch.data(), sch.size(), st);
   s->row_chunks.upload(rch.data(), rch.size(), st);
   s->inst_svec_chunk.upload(sfirst.data(), sfirst.size(), st);
@@ -356,6 +361,7 @@ void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
   s->inst_flag.alloc(count);
   s->inst_prec.alloc(count);
   s->iters.alloc(count);
+  s->iters64.alloc(count);
   s->n_active.alloc(1);
   s->blk_act32.alloc(s->nblk);
   s->blk_act64.alloc(s->nblk);
@@ -398,7 +404,7 @@ void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
   ad.atptr = s->atptr.p; ad.atrow = s->atrow.p; ad.atval = s->atval.p;
   ad.b = s->b.p; ad.C = s->C.p; ad.keep = s->keep.p; ad.norm_b = s->norm_b.p; ad.norm_C = s->norm_C.p;
   ad.X = s->X.p; ad.S = s->S.p; ad.sigma = s->sigma.p; ad.inst_active = s->inst_active.p;
-  ad.inst_flag = s->inst_flag.p; ad.inst_prec = s->inst_prec.p; ad.iters = s->iters.p; ad.stats = s->stats.p;
+  ad.inst_flag = s->inst_flag.p; ad.inst_prec = s->inst_prec.p; ad.iters = s->iters.p; ad.iters64 = s->iters64.p; ad.stats = s->stats.p;
   ad.part_svec = s->part_svec.p; ad.part_rows = s->part_rows.p; ad.n_active = s->n_active.p;
   ad.blk_inst = s->blk_inst.p; ad.blk_act32 = s->blk_act32.p; ad.blk_act64 = s->blk_act64.p;
   ad.blk_inv_sigma = s->blk_inv_sigma.p;
@@ -731,6 +737,11 @@ void strom::reset_instances(strom_solver* s, const std::vector<int>& inst) {
   copy_h2d(s->inst_flag.p, flag.data(), s->ninst, st);
   copy_h2d(s->inst_prec.p, prec.data(), s->ninst, st);
   copy_h2d(s->iters.p, it.data(), sizeof(int32_t) * s->ninst, st);
+  std::vector<int32_t> it64(s->ninst);
+  copy_d2h(it64.data(), s->iters64.p, sizeof(int32_t) * s->ninst, st);
+  STROM_CUDA(cudaStreamSynchronize(st));
+  for (int i : inst) it64[i] = 0;
+  copy_h2d(s->iters64.p, it64.data(), sizeof(int32_t) * s->ninst, st);
   STROM_CUDA(cudaStreamSynchronize(st));
 }
 
@@ -786,6 +797,7 @@ extern "C" int strom_solver_reset(strom_solver* s, int32_t i, const double* X0, 
     copy_h2d(s->inst_flag.p + i, &zero, 1, st);
     copy_h2d(s->inst_prec.p + i, &prec, 1, st);
     copy_h2d(s->iters.p + i, &zi, sizeof(int32_t), st);
+    copy_h2d(s->iters64.p + i, &zi, sizeof(int32_t), st);
     STROM_CUDA(cudaStreamSynchronize(st));
     return STROM_OK;
   });
