@@ -174,6 +174,20 @@ class Feeder:
         return relax_all(self.S, probs)
 
 
+def combine_ranks(dist, t, counts, device):
+    """Whole-job timing over replicas: the slowest rank's time and the sum of every rank's counts.
+
+    Replicas serve independent requests, so this host-side reduction is the
+    only exchange between ranks (none on the data path).
+    """
+    import torch
+    tt = torch.tensor([float(t)], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    cc = torch.tensor([float(c) for c in counts], device=device, dtype=torch.float64)
+    dist.all_reduce(cc)
+    return float(tt.item()), [int(round(c)) for c in cc.tolist()]
+
+
 def run_strom(a, rank, world):
     import numpy as np
     import torch
@@ -237,12 +251,7 @@ def run_strom(a, rank, world):
     ok = [f for f in finished if f[0].status == S.STROM_OK and f[1] is not None and f[1].xi == f[1].xi]
     solved = len(ok)
     if dist:
-        tt = torch.tensor([t], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
-        ss = torch.tensor([solved], device="cuda", dtype=torch.float64)
-        dist.all_reduce(ss)
-        solved = int(ss.item())
+        t, (solved,) = combine_ranks(dist, t, [solved], "cuda")
     value = solved / t
     svc = np.array([f[3] for f in ok]) if ok else np.array([np.nan])
     iters = np.array([f[0].iterations for f in ok]) if ok else np.array([0])
