@@ -305,6 +305,9 @@ __global__ void __launch_bounds__(NT) jacobi_psd_kernel(PsdArgs a, int list_star
         vs[idx] = (double)V[k * LDV + i];
       }
     }
+    // the recombination below scales V in place: every thread must have
+    // copied its share of the eigenvectors out first
+    __syncthreads();
   }
 
   // ---- eigen outputs (ascending eigenvalues, top eigenvector)
