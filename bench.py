@@ -50,8 +50,12 @@ def parse():
     ap.add_argument("--maxiter", type=int, default=6000)
     ap.add_argument("--plain", type=int, default=1, help="instances timed in the plain FP64 single-instance form")
     ap.add_argument("--cpu-budget", type=float, default=25.0)
-    ap.add_argument("--workload", default="served", choices=["served", "psd"],
-                    help="served: certified solves/s (default); psd: the 4096-block PSD-projection microbench")
+    ap.add_argument("--workload", default="served", choices=["served", "psd", "warm"],
+                    help="served: certified solves/s (default); psd: the 4096-block PSD-projection microbench; "
+                         "warm: nearest-neighbour warm starts from a database of solved pendulums")
+    ap.add_argument("--warm-grid", type=int, default=9, help="warm workload: database grid points per key axis")
+    ap.add_argument("--warm-queries", type=int, default=256, help="warm workload: batched queries")
+    ap.add_argument("--warm-single", type=int, default=4, help="warm workload: single-instance FP64 queries")
     ap.add_argument("--profile", default="none", choices=["none", "iterations", "psd"],
                     help="run a few launches of one case and exit (for ncu captures); prints no JSON")
     ap.add_argument("--precision", type=int, default=1, help="psd workload / profile: 0 = FP64, 1 = FP32")
@@ -558,6 +562,118 @@ def run_psd(a):
     print(json.dumps(line))
 
 
+def solve_status(S, sv):
+    """strom_solve, keeping the per-instance statuses when one instance hit NaN/Inf."""
+    from paper_2406_05846_gb300._native import StromError
+    try:
+        return sv.solve()
+    except StromError as e:
+        if e.status != -4:
+            raise
+        return e.status
+
+
+def run_warm(a):
+    """Data-driven warm starts (Sec. 5, inverted pendulum): a database of
+    solved pendulums on a grid of initial states (theta0, omega0) in
+    [-0.2, 0.2] x [-0.5, 0.5], solved offline by this solver; new initial
+    states (seeded, uniform over the same box) start from the convex
+    combination of their nearest stored solutions. Reported: throughput and
+    iterations of the same queries solved cold and warm (batched), and the
+    latency of single instances in the plain FP64 form."""
+    import numpy as np
+    import torch
+    import paper_2406_05846_gb300 as S
+    import workloads as wl
+    S.lib()
+    N, G, Q = a.horizon, a.warm_grid, a.warm_queries
+    scale = np.array([0.2, 0.5])
+    opts = dict(tol=1e-6, maxiter=a.maxiter, precision=S.STROM_PREC_MIXED, polish_eta=a.polish_eta, check_every=50)
+
+    def relax(params):
+        P = [wl.pendulum_problem(N=N, theta0=float(t), omega0=float(w)) for t, w in params]
+        return relax_all(S, P)
+
+    grid = [(t, w) for t in np.linspace(-0.2, 0.2, G) for w in np.linspace(-0.5, 0.5, G)]
+    Pg, sdg = relax(grid)
+    t0 = time.perf_counter()
+    dbs = S.Solver(sdg, **opts)
+    solve_status(S, dbs)
+    db_time = time.perf_counter() - t0
+    store = S.WarmStore(2, sdg[0].nsvec, len(grid))
+    stored = 0
+    for i, p in enumerate(grid):
+        if dbs.result(i).status == S.STROM_OK:
+            store.add_from_solver(dbs, i, np.array(p) / scale)
+            stored += 1
+    del dbs
+    rng = np.random.default_rng(np.random.PCG64(SEED + 777))
+    queries = np.column_stack([rng.uniform(-0.2, 0.2, Q), rng.uniform(-0.5, 0.5, Q)])
+    Pq, sdq = relax(queries)
+    stream = torch.cuda.current_stream()
+    clk = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clk.start()
+    out = {}
+    for mode in ("cold", "warm"):
+        sv = S.Solver(sdq, **opts)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        if mode == "warm":
+            for i, q in enumerate(queries):
+                sv.warm_start(i, store, q / scale)
+        solve_status(S, sv)
+        certs = sv.certify_batch(Pq)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        res = [sv.result(i) for i in range(Q)]
+        ok = [r.status == S.STROM_OK for r in res]
+        it = np.array([r.iterations for r in res])
+        bad = [[float(queries[i][0]), float(queries[i][1])] for i, r in enumerate(res) if r.status < 0]
+        out[mode] = {"solves_per_s": sum(ok) / t, "time_s": t, "converged": int(sum(ok)), "numerical": bad,
+                     "certified": int(sum(c.certified for c in certs)),
+                     "iterations_p50": float(np.percentile(it, 50)), "iterations_p99": float(np.percentile(it, 99)),
+                     "iterations_max": int(it.max()), "pobj": [r.pobj for r in res], "ok": ok}
+        del sv
+    pc, pw = np.array(out["cold"].pop("pobj")), np.array(out["warm"].pop("pobj"))
+    both = np.array(out["cold"].pop("ok")) & np.array(out["warm"].pop("ok"))
+    objdiff = float(np.max(np.abs(pw - pc)[both] / (1 + np.abs(pc[both]))))
+    # single instances, plain FP64 form, one at a time
+    single = {"cold": [], "warm": []}
+    iters1 = {"cold": [], "warm": []}
+    for i in range(min(a.warm_single, Q)):
+        for mode in ("cold", "warm"):
+            sv = S.Solver([sdq[i]], tol=1e-6, maxiter=a.maxiter, precision=S.STROM_PREC_FP64, check_every=50)
+            torch.cuda.synchronize()
+            ts = time.perf_counter()
+            if mode == "warm":
+                sv.warm_start(0, store, queries[i] / scale)
+            solve_status(S, sv)
+            sv.certify(0, Pq[i])
+            torch.cuda.synchronize()
+            single[mode].append(time.perf_counter() - ts)
+            iters1[mode].append(sv.result(0).iterations)
+            del sv
+    clocks = clk.stop()
+    line = {"metric": "certified solves/s with nearest-neighbour warm starts (pendulum N=%d)" % N,
+            "value": out["warm"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "higher_is_better": True, "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": "pendulum swing-up N=%d dt=0.1, initial state (theta0, omega0) ~ U([-0.2,0.2] x "
+                                   "[-0.5,0.5]) seeded, %d queries solved in one batch, KKT<=1e-6, certificate "
+                                   "per query; warm start = convex combination of the stored solutions of the "
+                                   "nearest database states (barycentric in their triangle)" % (N, Q),
+                       "database": "%dx%d grid over the same box, solved by this solver (%d converged, %.1f s)"
+                                   % (G, G, stored, db_time),
+                       "key_scale": scale.tolist()},
+            "cold": out["cold"], "warm": out["warm"], "speedup_batched": out["warm"]["solves_per_s"] /
+            max(1e-12, out["cold"]["solves_per_s"]), "objective_max_rel_diff_warm_vs_cold": objdiff,
+            "single_fp64": {"cold_latency_s": single["cold"], "warm_latency_s": single["warm"],
+                            "cold_iterations": iters1["cold"], "warm_iterations": iters1["warm"]},
+            "clocks": clocks}
+    print(json.dumps(line))
+
+
 def main():
     a = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -568,6 +684,8 @@ def main():
         run_reference(a, rank, world)
     elif a.workload == "psd":
         run_psd(a)
+    elif a.workload == "warm":
+        run_warm(a)
     else:
         run_strom(a, rank, world)
 

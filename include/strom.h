@@ -248,6 +248,61 @@ int strom_batch_step(strom_batch* b, int32_t iters, void* stream, int32_t* n_run
 int strom_batch_poll(strom_batch* b, uint64_t ticket, strom_result* r, strom_certificate* c, double* latency_s,
                      double* service_s);
 /* ------------------------------------------------------------------------
+ * Data-driven warm starts (Sec. 5, inverted pendulum initialised by a
+ * nearest-neighbour search over stored solutions). A store holds solved
+ * states (X, S, sigma) of one SDP structure in device memory (capacity x 2 x
+ * nsvec doubles), each under a key of key_dim doubles: the parameters that
+ * tell instances apart (e.g. the initial state), scaled by the caller so
+ * that Euclidean distance compares them. A new instance starts from a convex
+ * combination of stored states, chosen as follows. The stored keys are
+ * ranked by distance to the new key (ties: lower index first) and the first
+ * min(key_dim + 1, count) are the neighbours. A key equal to a stored key
+ * takes that state alone. When there are key_dim + 1 neighbours, their keys
+ * span a non-degenerate simplex and the new key lies in it (barycentric
+ * coordinates >= -1e-12), the weights are those barycentric coordinates
+ * (clipped at 0, renormalised): for keys on a grid and key_dim = 2 this is
+ * the triangle of a Delaunay triangulation. Otherwise the weights are
+ * proportional to 1 / distance. X0 = sum_j w_j X_j, S0 = sum_j w_j S_j,
+ * y = 0, and sigma0 = prod_j sigma_j^{w_j}.
+ * ---------------------------------------------------------------------- */
+#define STROM_WARM_MAX_KEY 8
+typedef struct strom_warm strom_warm;
+
+/* The neighbour selection alone, on a host table keys [n x key_dim]
+ * (row-major): idx, wt have room for key_dim + 1 entries; *k receives the
+ * number used (0 when n = 0). Host only; no GPU needed. */
+int strom_warm_select(const double* keys, int32_t n, int32_t key_dim, const double* key, int32_t* idx, double* wt,
+                      int32_t* k);
+/* key_dim 1..STROM_WARM_MAX_KEY, nsvec >= 1, capacity >= 1; allocates the
+ * device store on the current device. Errors: INVALID, OOM, CUDA. */
+int strom_warm_create(int32_t key_dim, int64_t nsvec, int32_t capacity, strom_warm** out);
+void strom_warm_destroy(strom_warm* w);
+/* Entries stored (-1 for a NULL store). */
+int32_t strom_warm_count(const strom_warm* w);
+/* Adds a state from host arrays X, S [nsvec] with sigma > 0; *index
+ * (nullable) receives its index. INVALID when the store is full. */
+int strom_warm_add(strom_warm* w, const double* key, const double* X, const double* S, double sigma, int32_t* index);
+/* Adds the current (X, S, sigma) of instance i of a solver by device copies.
+ * INVALID when the store is full or the instance's svec length differs. */
+int strom_warm_add_from_solver(strom_warm* w, const strom_solver* s, int32_t i, const double* key, int32_t* index);
+/* strom_warm_select over the stored keys. */
+int strom_warm_query(const strom_warm* w, const double* key, int32_t* idx, double* wt, int32_t* k);
+/* Host copies of entry j (any output may be NULL). */
+int strom_warm_get(const strom_warm* w, int32_t j, double* key, double* X, double* S, double* sigma);
+/* Resets instance i of a solver to the warm start for key (combined on the
+ * device); an empty store leaves the cold start X = S = y = 0, sigma0. */
+int strom_solver_warm_start(strom_solver* s, int32_t i, const strom_warm* w, const double* key);
+/* Attaches a store to a batch (NULL detaches). Requests submitted with a
+ * key start, at admission, from the store's combination for their key; with
+ * record != 0 each keyed request that meets tol is added to the store at
+ * retirement while it has room. The store must outlive its attachment. */
+int strom_batch_set_warm(strom_batch* b, strom_warm* w, int32_t record);
+/* strom_batch_submit with a warm-start key (key_dim doubles of the attached
+ * store); INVALID when no store is attached. */
+int strom_batch_submit_keyed(strom_batch* b, const strom_sdp* sdp, const strom_problem* problem, const double* key,
+                             uint64_t* ticket);
+
+/* ------------------------------------------------------------------------
  * Kernel-level entry points for parity tests (device pointers, caller's
  * stream). They use the solver's uploaded operator of the whole batch: x has
  * length strom_solver_nsvec_total, y and r have length strom_solver_m_total.

@@ -13,6 +13,8 @@ Contents, each following the paper directly:
   certify    rank-1 test (Theorem 1 iii), extraction heuristic (Sec. 2.2),
              valid lower bound (eq. valid-lowerbound), suboptimality gap
              (eq. suboptimality-gap), R_beta (Theorem of App. C)
+  warm       nearest-neighbour warm start from stored solutions (Sec. 5,
+             inverted pendulum)
 
 Parity status: every function is pinned by tests under tests/ against the
 paper's worked identities, closed forms, invariants or brute force, except

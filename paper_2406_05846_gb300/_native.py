@@ -9,6 +9,7 @@ LIB_PATH = os.path.join(HERE, "libstrom.so")
 
 STROM_OK, STROM_MAXITER, STROM_PENDING = 0, 1, 2
 STROM_PREC_FP64, STROM_PREC_FP32, STROM_PREC_MIXED = 0, 1, 2
+STROM_WARM_MAX_KEY = 8
 
 
 class strom_poly(C.Structure):
@@ -96,6 +97,17 @@ SIGNATURES = {
     "strom_batch_step": (C.c_int, [P, C.c_int32, P, PI32, PI32]),
     "strom_batch_poll": (C.c_int, [P, C.c_uint64, C.POINTER(strom_result), C.POINTER(strom_certificate),
                                    PD, PD]),
+    "strom_warm_select": (C.c_int, [PD, C.c_int32, C.c_int32, PD, PI32, PD, PI32]),
+    "strom_warm_create": (C.c_int, [C.c_int32, C.c_int64, C.c_int32, C.POINTER(P)]),
+    "strom_warm_destroy": (None, [P]),
+    "strom_warm_count": (C.c_int32, [P]),
+    "strom_warm_add": (C.c_int, [P, PD, PD, PD, C.c_double, PI32]),
+    "strom_warm_add_from_solver": (C.c_int, [P, P, C.c_int32, PD, PI32]),
+    "strom_warm_query": (C.c_int, [P, PD, PI32, PD, PI32]),
+    "strom_warm_get": (C.c_int, [P, C.c_int32, PD, PD, PD, PD]),
+    "strom_solver_warm_start": (C.c_int, [P, C.c_int32, P, PD]),
+    "strom_batch_set_warm": (C.c_int, [P, P, C.c_int32]),
+    "strom_batch_submit_keyed": (C.c_int, [P, P, P, PD, C.POINTER(C.c_uint64)]),
     "strom_psd_plan_create": (C.c_int, [PI64, PI32, C.c_int32, C.c_int32, C.POINTER(P)]),
     "strom_psd_plan_destroy": (None, [P]),
     "strom_psd_execute": (C.c_int, [P, P, P, P, P]),

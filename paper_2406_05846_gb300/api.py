@@ -192,6 +192,11 @@ class Solver:
         ps = None if S0 is None else _ptr(np.ascontiguousarray(S0, np.float64), C.c_double)
         check(lib().strom_solver_reset(self.handle, i, px, ps, float(sigma)), "strom_solver_reset")
 
+    def warm_start(self, i, store: WarmStore, key):
+        """Reset instance i to the store's warm start for key (cold when the store is empty)."""
+        _, pk = _key(key)
+        check(lib().strom_solver_warm_start(self.handle, i, store.handle, pk), "strom_solver_warm_start")
+
     def result(self, i=0) -> Result:
         r = N.strom_result()
         check(lib().strom_get_result(self.handle, i, C.byref(r)), "strom_get_result")
@@ -249,6 +254,73 @@ class Solver:
         check(lib().strom_kernel_solve(self.handle, r_ptr, y_ptr, stream), "strom_kernel_solve")
 
 
+def _key(key):
+    k = np.ascontiguousarray(np.atleast_1d(np.asarray(key, np.float64)))
+    return k, _ptr(k, C.c_double)
+
+
+def warm_select(keys, key):
+    """Neighbour indices and convex weights of `key` among the rows of `keys` (host only)."""
+    keys = np.ascontiguousarray(np.atleast_2d(np.asarray(keys, np.float64)))
+    k, pk = _key(key)
+    d = k.size
+    if keys.size == 0:
+        keys = np.zeros((0, d))
+    if keys.shape[1] != d:
+        raise ValueError("key dimension differs from the stored keys'")
+    idx, wt, n = np.zeros(d + 1, np.int32), np.zeros(d + 1), C.c_int32()
+    check(lib().strom_warm_select(_ptr(keys, C.c_double), keys.shape[0], d, pk, _ptr(idx, C.c_int32),
+                                  _ptr(wt, C.c_double), C.byref(n)), "strom_warm_select")
+    return idx[:n.value].copy(), wt[:n.value].copy()
+
+
+class WarmStore:
+    """strom_warm: solved states in device memory for data-driven warm starts."""
+
+    def __init__(self, key_dim: int, nsvec: int, capacity: int):
+        h = C.c_void_p()
+        check(lib().strom_warm_create(key_dim, nsvec, capacity, C.byref(h)), "strom_warm_create")
+        self.handle = h
+        self.key_dim, self.nsvec, self.capacity = key_dim, nsvec, capacity
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib().strom_warm_destroy(self.handle)
+            self.handle = None
+
+    def __len__(self):
+        return lib().strom_warm_count(self.handle)
+
+    def add(self, key, X, S, sigma) -> int:
+        _, pk = _key(key)
+        X = np.ascontiguousarray(X, np.float64)
+        S = np.ascontiguousarray(S, np.float64)
+        j = C.c_int32()
+        check(lib().strom_warm_add(self.handle, pk, _ptr(X, C.c_double), _ptr(S, C.c_double), float(sigma),
+                                   C.byref(j)), "strom_warm_add")
+        return j.value
+
+    def add_from_solver(self, solver: "Solver", i: int, key) -> int:
+        _, pk = _key(key)
+        j = C.c_int32()
+        check(lib().strom_warm_add_from_solver(self.handle, solver.handle, i, pk, C.byref(j)),
+              "strom_warm_add_from_solver")
+        return j.value
+
+    def query(self, key):
+        _, pk = _key(key)
+        idx, wt, n = np.zeros(self.key_dim + 1, np.int32), np.zeros(self.key_dim + 1), C.c_int32()
+        check(lib().strom_warm_query(self.handle, pk, _ptr(idx, C.c_int32), _ptr(wt, C.c_double), C.byref(n)),
+              "strom_warm_query")
+        return idx[:n.value].copy(), wt[:n.value].copy()
+
+    def get(self, j):
+        key, X, S, sg = np.empty(self.key_dim), np.empty(self.nsvec), np.empty(self.nsvec), C.c_double()
+        check(lib().strom_warm_get(self.handle, j, _ptr(key, C.c_double), _ptr(X, C.c_double),
+                                   _ptr(S, C.c_double), C.byref(sg)), "strom_warm_get")
+        return key, X, S, sg.value
+
+
 class Batch:
     """strom_batch: continuous batching of solve requests over `slots` solver slots."""
 
@@ -270,6 +342,18 @@ class Batch:
         ps = None if S0 is None else _ptr(np.ascontiguousarray(S0, np.float64), C.c_double)
         check(lib().strom_batch_submit(self.handle, sdp.handle, problem.handle if problem else None, px, ps,
                                        C.byref(t)), "strom_batch_submit")
+        return t.value
+
+    def set_warm(self, store: "WarmStore | None", record=False):
+        check(lib().strom_batch_set_warm(self.handle, store.handle if store is not None else None, int(bool(record))),
+              "strom_batch_set_warm")
+        self.warm = store     # keeps the store alive while attached
+
+    def submit_keyed(self, sdp: Sdp, key, problem: Problem | None = None) -> int:
+        t = C.c_uint64()
+        _, pk = _key(key)
+        check(lib().strom_batch_submit_keyed(self.handle, sdp.handle, problem.handle if problem else None, pk,
+                                             C.byref(t)), "strom_batch_submit_keyed")
         return t.value
 
     def step(self, iters: int, stream=None):

@@ -12,8 +12,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libstrom.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU = ["psd.cu", "factor.cu", "admm.cu", "solver.cu", "serve.cu", "noalloc.cu"]
-CPP = ["relax.cpp", "capi.cpp", "certify.cpp"]
+CU = ["psd.cu", "factor.cu", "admm.cu", "solver.cu", "serve.cu", "noalloc.cu", "warm.cu"]
+CPP = ["relax.cpp", "capi.cpp", "certify.cpp", "warm_select.cpp"]
 
 
 def _nvcc():
@@ -38,13 +38,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
     jobs = []
+    # host code is compiled without FMA contraction so that x86 and Arm
+    # builds give bit-identical host results
     for f in CU:
         o = os.path.join(BUILD, f + ".o")
-        jobs.append([nvcc, *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
+        jobs.append([nvcc, *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",
                      "-c", os.path.join(CSRC, f), "-o", o])
     for f in CPP:
         o = os.path.join(BUILD, f + ".o")
-        jobs.append(["g++", "-std=c++17", "-O2", "-fPIC", "-Wall", "-I/usr/local/cuda/include",
+        jobs.append(["g++", "-std=c++17", "-O2", "-fPIC", "-Wall", "-ffp-contract=off", "-I/usr/local/cuda/include",
                      "-c", os.path.join(CSRC, f), "-o", o])
 
     def run(cmd):

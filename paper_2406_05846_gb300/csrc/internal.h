@@ -74,6 +74,10 @@ void certify_one(const Problem& p, const std::vector<int32_t>& bn, const std::ve
 
 std::vector<std::vector<uint8_t>> monomial_basis(int nv, int d);
 
+// warm-start neighbours of key among n stored keys (row-major n x d): fills
+// idx / wt (length d + 1) and returns how many are used (warm_select.cpp)
+int warm_select(const double* keys, int n, int d, const double* key, int32_t* idx, double* wt);
+
 }  // namespace strom
 
 struct strom_problem { strom::Problem p; };

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "solver_impl.cuh"
+#include "warm.cuh"
 
 namespace {
 
@@ -21,6 +22,7 @@ double now_s() {
 struct Request {
   uint64_t ticket = 0;
   std::vector<double> val, b, C, X0, S0;
+  std::vector<double> key;  // warm-start key (empty: not keyed)
   bool has_prob = false;
   strom::Problem prob;
   double t_submit = 0.0;
@@ -52,6 +54,8 @@ struct strom_batch {
   std::vector<Request> slot_req;
   std::unordered_map<uint64_t, Done> done;
   uint64_t next = 1;
+  strom_warm* warm = nullptr;  // warm-start store for keyed requests (not owned)
+  bool record = false;         // add converged keyed requests to it
   ~strom_batch() { strom_solver_destroy(s); }
 };
 
@@ -105,10 +109,23 @@ void admit(strom_batch* B) {
   if (adm.empty()) return;
   factor_instances(s, adm);
   reset_instances(s, adm);
+  std::vector<double> wsig(s->ninst, 0.0);
+  bool any_warm = false;
   for (int i : adm) {
     const Request& rq = B->slot_req[i];
     if (!rq.X0.empty()) copy_h2d(s->X.p + s->svec_off[i], rq.X0.data(), sizeof(double) * B->nsvec, s->stream);
     if (!rq.S0.empty()) copy_h2d(s->S.p + s->svec_off[i], rq.S0.data(), sizeof(double) * B->nsvec, s->stream);
+    if (!rq.key.empty() && B->warm &&
+        warm_apply(B->warm, rq.key.data(), s->X.p + s->svec_off[i], s->S.p + s->svec_off[i], &wsig[i], s->stream))
+      any_warm = true;
+  }
+  if (any_warm) {
+    std::vector<double> sg(s->ninst);
+    copy_d2h(sg.data(), s->sigma.p, sizeof(double) * s->ninst, s->stream);
+    STROM_CUDA(cudaStreamSynchronize(s->stream));
+    for (int i : adm)
+      if (wsig[i] > 0) sg[i] = wsig[i];
+    copy_h2d(s->sigma.p, sg.data(), sizeof(double) * s->ninst, s->stream);
   }
   STROM_CUDA(cudaStreamSynchronize(s->stream));
 }
@@ -153,6 +170,8 @@ void retire(strom_batch* B) {
                   topX.data(), lamZ.data(), st[4], 1e-4, 1e-2, &d.c, nullptr, nullptr);
       d.has_c = true;
     }
+    if (flag[i] == 1 && B->warm && B->record && !rq.key.empty())
+      warm_append(B->warm, rq.key.data(), s->X.p + s->svec_off[i], s->S.p + s->svec_off[i], sg[i], s->stream);
     d.latency = t - rq.t_submit;
     d.service = t - rq.t_admit;
     B->done[rq.ticket] = d;
@@ -198,8 +217,10 @@ extern "C" int strom_batch_create(const strom_sdp* tmpl, int32_t slots, const st
 
 extern "C" void strom_batch_destroy(strom_batch* b) { delete b; }
 
-extern "C" int strom_batch_submit(strom_batch* B, const strom_sdp* sdp, const strom_problem* problem, const double* X0,
-                                  const double* S0, uint64_t* ticket) {
+namespace {
+
+int submit(strom_batch* B, const strom_sdp* sdp, const strom_problem* problem, const double* X0, const double* S0,
+           const double* key, uint64_t* ticket) {
   return guard([&]() -> int {
     if (!B || !sdp || !sdp->s || !ticket) throw StatusError(STROM_ERR_INVALID, "strom_batch_submit: bad arguments");
     const Sdp& q = *sdp->s;
@@ -226,9 +247,42 @@ extern "C" int strom_batch_submit(strom_batch* B, const strom_sdp* sdp, const st
     }
     if (X0) rq.X0.assign(X0, X0 + q.nsvec);
     if (S0) rq.S0.assign(S0, S0 + q.nsvec);
+    if (key) {
+      if (!B->warm) throw StatusError(STROM_ERR_INVALID, "strom_batch_submit_keyed: no warm-start store attached");
+      for (int t = 0; t < B->warm->d; ++t)
+        if (!std::isfinite(key[t])) throw StatusError(STROM_ERR_INVALID, "strom_batch_submit_keyed: non-finite key");
+      rq.key.assign(key, key + B->warm->d);
+    }
     rq.t_submit = now_s();
     *ticket = rq.ticket;
     B->queue.push_back(std::move(rq));
+    return STROM_OK;
+  });
+}
+
+}  // namespace
+
+extern "C" int strom_batch_submit(strom_batch* B, const strom_sdp* sdp, const strom_problem* problem, const double* X0,
+                                  const double* S0, uint64_t* ticket) {
+  return submit(B, sdp, problem, X0, S0, nullptr, ticket);
+}
+
+extern "C" int strom_batch_submit_keyed(strom_batch* B, const strom_sdp* sdp, const strom_problem* problem,
+                                        const double* key, uint64_t* ticket) {
+  if (!key) {
+    set_error("strom_batch_submit_keyed: null key");
+    return STROM_ERR_INVALID;
+  }
+  return submit(B, sdp, problem, nullptr, nullptr, key, ticket);
+}
+
+extern "C" int strom_batch_set_warm(strom_batch* B, strom_warm* w, int32_t record) {
+  return guard([&]() -> int {
+    if (!B) throw StatusError(STROM_ERR_INVALID, "strom_batch_set_warm: null batch");
+    if (w && w->nsvec != B->nsvec)
+      throw StatusError(STROM_ERR_INVALID, "strom_batch_set_warm: the store's svec length differs from the batch's");
+    B->warm = w;
+    B->record = w && record != 0;
     return STROM_OK;
   });
 }

@@ -101,7 +101,7 @@ def _cayley(c0, s0, w, c1, s1, hw):
 # pendulum swing-up: state (c, s, w), control u
 # --------------------------------------------------------------------------
 def pendulum_problem(N: int = 10, dt: float = 0.1, theta0: float = 0.1, g_l: float = 9.81,
-                     u_max: float = 2.0, w_max: float = 4.0) -> Problem:
+                     u_max: float = 2.0, w_max: float = 4.0, omega0: float = 0.0) -> Problem:
     """Pendulum: theta from hanging, c = cos(theta), s = sin(theta), w = theta-dot.
 
     Rescaled variables: w = w_max * W, u = u_max * U.
@@ -111,7 +111,7 @@ def pendulum_problem(N: int = 10, dt: float = 0.1, theta0: float = 0.1, g_l: flo
       bounds   : 1 - U^2 >= 0, 1 - W_k^2 >= 0
       cost     : sum_{k=0}^{N-1} 10 (1 + c_k)^2 + w_k^2 + 0.1 u_k^2
                  + 10 (1 + c_N)^2 + w_N^2     (terminal weight Pf = 1)
-      initial  : c_0 = cos(theta0), s_0 = sin(theta0), w_0 = 0 (clique 1)
+      initial  : c_0 = cos(theta0), s_0 = sin(theta0), w_0 = omega0 (clique 1)
     """
     nv = 7
     C0, S0, W0, U, C1, S1, W1 = (Poly.var(nv, i) for i in range(nv))
@@ -126,7 +126,7 @@ def pendulum_problem(N: int = 10, dt: float = 0.1, theta0: float = 0.1, g_l: flo
         e4 = C1 * C1 + S1 * S1 - 1.0
         h = [e1, e2, e3, e4]
         if k == 1:
-            h += [C0 - np.cos(theta0), S0 - np.sin(theta0), W0 - 0.0]
+            h += [C0 - np.cos(theta0), S0 - np.sin(theta0), W0 - omega0 / w_max]
         g = [1.0 - U * U, 1.0 - W1 * W1]
         raw.append((f, g, h))
     fscale = 1.0 / max(f.max_abs_coef() for f, _, _ in raw)
