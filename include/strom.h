@@ -111,6 +111,53 @@ int strom_sdp_export(const strom_sdp* s, int32_t* block_n, int64_t* block_off, i
                      double* b, int8_t* row_kind, int32_t* row_clique);
 void strom_sdp_destroy(strom_sdp* s);
 
+/* An SDP given by arrays in the layout strom_sdp_export writes, e.g. the
+ * relaxation of Sec. 2.3 built by another implementation. Blocks are ordered
+ * by clique, each clique led by its moment block of size s(2 dx + du, 2);
+ * svec offsets are the running sums of n (n + 1) / 2. Rows are ordered by
+ * clique; every row stays inside its clique's blocks except consensus rows,
+ * which may also reach the next clique's moment block (the chain structure
+ * of Definition 1); inside a clique the consensus rows come after every row
+ * other than A_mom rows. Each A_mom row is s_p X_p - s_r X_r = 0 with b = 0,
+ * the representative r first (column order) and s = 1 on the diagonal,
+ * 1/sqrt(2) off it (svec scaling), and no entry is the duplicate of two rows.
+ * The data of the y-solve's star elimination and clique groups are derived
+ * from these rows. Arrays are copied. Errors: INVALID (with the first rule
+ * broken in strom_last_error), OOM. */
+typedef struct {
+  int32_t N, dx, du;                /* horizon, state and control sizes: clique vars (x_{k-1}, u_{k-1}, x_k) */
+  int32_t nblocks;
+  const int32_t* block_n;           /* [nblocks] sizes 1..160 */
+  const int8_t* block_kind;         /* [nblocks] 0 = moment, 1 = localizing */
+  const int32_t* block_clique;      /* [nblocks] */
+  const int32_t* block_index;       /* [nblocks] localizing constraint index in its clique, -1 for moment;
+                                       NULL: localizing blocks are numbered in order */
+  const double* C;                  /* [nsvec] */
+  int64_t m;                        /* rows */
+  const int64_t* rowptr;            /* [m + 1] CSR, rowptr[0] = 0 */
+  const int32_t* col;               /* [nnz] strictly increasing inside a row */
+  const double* val;                /* [nnz] */
+  const double* b;                  /* [m] */
+  const int8_t* row_kind;           /* [m] STROM_ROW_* */
+  const int32_t* row_clique;        /* [m] */
+} strom_sdp_desc;
+int strom_sdp_import(const strom_sdp_desc* d, strom_sdp** out);
+
+/* The star elimination the y-solve applies to the A_mom rows (each ties a
+ * duplicate entry p of a moment matrix to the representative r of its
+ * monomial): one class per representative with duplicates, cliques in
+ * order and inside a clique in order of the class's first A_mom row. Per
+ * class: rep (svec position), c = s_r^2, dsum = sum of 1/s_p^2 over its
+ * rows, ptr [nclass + 1] into row / inv_s2 (its A_mom rows and their
+ * 1/s_p^2). omega [nsvec]: weights of the Gram A_o diag(omega) A_o^T of the
+ * other rows (1 / (occurrences s_r^2) at representatives, 0 at duplicates,
+ * 1 on localizing blocks); inv_rep_s [nsvec]: 1/s_r at representatives of
+ * moment blocks, else 0. *nclass, *nstar receive the sizes (call once with
+ * NULL arrays to size them); any pointer may be NULL. */
+int strom_sdp_star_export(const strom_sdp* s, int64_t* nclass, int64_t* nstar, int64_t* rep, double* c,
+                          double* dsum, int32_t* ptr, int64_t* row, double* inv_s2, double* omega,
+                          double* inv_rep_s);
+
 /* ------------------------------------------------------------------------
  * Solver: sGS-ADMM (Algorithm 1) on a batch of independent SDPs, all on the
  * current CUDA device. Creation uploads the data, removes linearly dependent

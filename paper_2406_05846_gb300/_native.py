@@ -31,6 +31,15 @@ class strom_sdp_info(C.Structure):
                 ("m", C.c_int64), ("nnz", C.c_int64), ("rows_by_kind", C.c_int64 * 5)]
 
 
+class strom_sdp_desc(C.Structure):
+    _fields_ = [("N", C.c_int32), ("dx", C.c_int32), ("du", C.c_int32), ("nblocks", C.c_int32),
+                ("block_n", C.POINTER(C.c_int32)), ("block_kind", C.POINTER(C.c_int8)),
+                ("block_clique", C.POINTER(C.c_int32)), ("block_index", C.POINTER(C.c_int32)),
+                ("C", C.POINTER(C.c_double)), ("m", C.c_int64), ("rowptr", C.POINTER(C.c_int64)),
+                ("col", C.POINTER(C.c_int32)), ("val", C.POINTER(C.c_double)), ("b", C.POINTER(C.c_double)),
+                ("row_kind", C.POINTER(C.c_int8)), ("row_clique", C.POINTER(C.c_int32))]
+
+
 class strom_options(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxiter", C.c_int32), ("sigma0", C.c_double), ("tau", C.c_double),
                 ("sigma_every", C.c_int32), ("sigma_ratio", C.c_double), ("sigma_factor", C.c_double),
@@ -69,6 +78,8 @@ SIGNATURES = {
     "strom_sdp_info_get": (C.c_int, [P, C.POINTER(strom_sdp_info)]),
     "strom_sdp_export": (C.c_int, [P, PI32, PI64, PI8, PI32, PD, PI64, PI32, PD, PD, PI8, PI32]),
     "strom_sdp_destroy": (None, [P]),
+    "strom_sdp_import": (C.c_int, [C.POINTER(strom_sdp_desc), C.POINTER(P)]),
+    "strom_sdp_star_export": (C.c_int, [P, PI64, PI64, PI64, PD, PD, PI32, PI64, PD, PD, PD]),
     "strom_options_default": (None, [C.POINTER(strom_options)]),
     "strom_solver_create": (C.c_int, [C.POINTER(P), C.c_int32, C.POINTER(strom_options), C.POINTER(P)]),
     "strom_solver_destroy": (None, [P]),

@@ -77,11 +77,58 @@ class SdpArrays:
     row_clique: np.ndarray
 
 
+@dataclass
+class StarData:
+    rep: np.ndarray
+    c: np.ndarray
+    dsum: np.ndarray
+    ptr: np.ndarray
+    row: np.ndarray
+    inv_s2: np.ndarray
+    omega: np.ndarray
+    inv_rep_s: np.ndarray
+
+
 class Sdp:
     def __init__(self, handle):
         self.handle = handle
         self.info = N.strom_sdp_info()
         check(lib().strom_sdp_info_get(handle, C.byref(self.info)), "strom_sdp_info_get")
+
+    @classmethod
+    def from_arrays(cls, N_, dx, du, block_n, block_kind, block_clique, C_, rowptr, col, val, b, row_kind,
+                    row_clique, block_index=None) -> "Sdp":
+        """strom_sdp_import: an SDP given by arrays in the layout of export()."""
+        keep = [np.ascontiguousarray(block_n, np.int32), np.ascontiguousarray(block_kind, np.int8),
+                np.ascontiguousarray(block_clique, np.int32),
+                None if block_index is None else np.ascontiguousarray(block_index, np.int32),
+                np.ascontiguousarray(C_, np.float64), np.ascontiguousarray(rowptr, np.int64),
+                np.ascontiguousarray(col, np.int32), np.ascontiguousarray(val, np.float64),
+                np.ascontiguousarray(b, np.float64), np.ascontiguousarray(row_kind, np.int8),
+                np.ascontiguousarray(row_clique, np.int32)]
+        bn, bk, bc, bi, cc, rp, co, va, bb, rk, rc = keep
+        d = N.strom_sdp_desc(int(N_), int(dx), int(du), bn.size, _ptr(bn, C.c_int32), _ptr(bk, C.c_int8),
+                             _ptr(bc, C.c_int32), None if bi is None else _ptr(bi, C.c_int32),
+                             _ptr(cc, C.c_double), bb.size, _ptr(rp, C.c_int64), _ptr(co, C.c_int32),
+                             _ptr(va, C.c_double), _ptr(bb, C.c_double), _ptr(rk, C.c_int8), _ptr(rc, C.c_int32))
+        h = C.c_void_p()
+        check(lib().strom_sdp_import(C.byref(d), C.byref(h)), "strom_sdp_import")
+        return cls(h)
+
+    def star_data(self) -> StarData:
+        """strom_sdp_star_export: the star elimination and Gram weights used by the y-solve."""
+        nc, ns = C.c_int64(), C.c_int64()
+        check(lib().strom_sdp_star_export(self.handle, C.byref(nc), C.byref(ns), *([None] * 8)),
+              "strom_sdp_star_export")
+        o = StarData(np.empty(nc.value, np.int64), np.empty(nc.value), np.empty(nc.value),
+                     np.empty(nc.value + 1, np.int32), np.empty(ns.value, np.int64), np.empty(ns.value),
+                     np.empty(self.nsvec), np.empty(self.nsvec))
+        check(lib().strom_sdp_star_export(self.handle, None, None, _ptr(o.rep, C.c_int64), _ptr(o.c, C.c_double),
+                                          _ptr(o.dsum, C.c_double), _ptr(o.ptr, C.c_int32),
+                                          _ptr(o.row, C.c_int64), _ptr(o.inv_s2, C.c_double),
+                                          _ptr(o.omega, C.c_double), _ptr(o.inv_rep_s, C.c_double)),
+              "strom_sdp_star_export")
+        return o
 
     def __del__(self):
         if getattr(self, "handle", None):

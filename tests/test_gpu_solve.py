@@ -94,3 +94,23 @@ def test_certificate_matches_oracle():
     assert abs(c.phat - oc.phat) <= 1e-9 * (1 + abs(oc.phat))
     assert c.xi >= -1e-12
     assert c.lower_bound <= c.phat + 1e-9
+
+
+def test_imported_sdp_solves_like_the_built_one():
+    # the oracle's SDP, imported by arrays, gives the same solve as the
+    # library's own relaxation of the same problem
+    S = lib()
+    p = wl.pendulum_problem(N=4, theta0=0.11, omega0=0.2)
+    o = OR.relax(p)
+    im = S.Sdp.from_arrays(p.N, p.dx, p.du, [b.n for b in o.blocks], [0 if b.kind == "M" else 1 for b in o.blocks],
+                           [b.clique for b in o.blocks], o.C, o.A.indptr, o.A.indices, o.A.data, o.b, o.row_kind,
+                           o.row_clique, block_index=[b.index for b in o.blocks])
+    built = S.Problem(p).relax()
+    res = []
+    for sd in (built, im):
+        sv = S.Solver([sd], tol=1e-6, maxiter=20000, precision=S.STROM_PREC_FP64, check_every=10)
+        assert sv.solve() == S.STROM_OK
+        res.append(sv.result(0))
+    assert np.array_equal(S.Solver([built]).kept_rows(0), S.Solver([im]).kept_rows(0))
+    assert abs(res[0].pobj - res[1].pobj) <= 1e-6 * (1 + abs(res[0].pobj))
+    assert abs(res[0].iterations - res[1].iterations) <= max(20, res[0].iterations // 10)
