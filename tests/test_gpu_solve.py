@@ -114,3 +114,22 @@ def test_imported_sdp_solves_like_the_built_one():
     assert np.array_equal(S.Solver([built]).kept_rows(0), S.Solver([im]).kept_rows(0))
     assert abs(res[0].pobj - res[1].pobj) <= 1e-6 * (1 + abs(res[0].pobj))
     assert abs(res[0].iterations - res[1].iterations) <= max(20, res[0].iterations // 10)
+
+
+def test_batch_iterations_are_repeatable():
+    # two solvers on the same 64 instances agree bit for bit after 100
+    # iterations in mixed precision (eigensolver warm starts included): no
+    # kernel of the iteration reads data another thread may still change
+    S = lib()
+    rng = np.random.default_rng(9)
+    probs = [wl.pendulum_problem(N=6, theta0=float(t), omega0=float(w))
+             for t, w in zip(rng.uniform(-0.2, 0.2, 64), rng.uniform(-0.5, 0.5, 64))]
+    sdps = [S.Problem(p).relax() for p in probs]
+    a = S.Solver(sdps, tol=1e-12, maxiter=100, precision=S.STROM_PREC_MIXED, check_every=20)
+    b = S.Solver(sdps, tol=1e-12, maxiter=100, precision=S.STROM_PREC_MIXED, check_every=20)
+    a.step(100)
+    b.step(100)
+    for i in range(len(sdps)):
+        xa, sa, ya = a.state(i)
+        xb, sb, yb = b.state(i)
+        assert np.array_equal(xa, xb) and np.array_equal(sa, sb) and np.array_equal(ya, yb), i
