@@ -50,9 +50,13 @@ def parse():
     ap.add_argument("--maxiter", type=int, default=6000)
     ap.add_argument("--plain", type=int, default=1, help="instances timed in the plain FP64 single-instance form")
     ap.add_argument("--cpu-budget", type=float, default=25.0)
-    ap.add_argument("--workload", default="served", choices=["served", "psd", "warm"],
+    ap.add_argument("--workload", default="served", choices=["served", "psd", "warm", "poisson"],
                     help="served: certified solves/s (default); psd: the 4096-block PSD-projection microbench; "
-                         "warm: nearest-neighbour warm starts from a database of solved pendulums")
+                         "warm: nearest-neighbour warm starts from a database of solved pendulums; "
+                         "poisson: open-loop Poisson arrivals served cold and with warm starts from solved requests")
+    ap.add_argument("--rate", type=float, default=40.0, help="poisson workload: arrivals per second")
+    ap.add_argument("--duration", type=float, default=12.0, help="poisson workload: seconds of arrivals")
+    ap.add_argument("--step-iters", type=int, default=40, help="poisson workload: iterations per serving step")
     ap.add_argument("--warm-grid", type=int, default=9, help="warm workload: database grid points per key axis")
     ap.add_argument("--warm-queries", type=int, default=256, help="warm workload: batched queries")
     ap.add_argument("--warm-single", type=int, default=4, help="warm workload: single-instance FP64 queries")
@@ -674,6 +678,99 @@ def run_warm(a):
     print(json.dumps(line))
 
 
+def run_poisson(a):
+    """Open-loop serving: pendulum requests (N=10, (theta0, omega0) uniform in
+    [-0.2, 0.2] x [-0.5, 0.5]) arrive as a seeded Poisson process of rate
+    --rate for --duration seconds and are served by continuous batching.
+    Run twice on the same arrivals: cold starts, and warm starts from the
+    nearest requests already solved (each converged request is recorded in a
+    device-resident store keyed by its initial state; the store starts
+    empty). Latency = arrival to the host seeing the result, queueing
+    included."""
+    import numpy as np
+    import torch
+    import paper_2406_05846_gb300 as S
+    import workloads as wl
+    S.lib()
+    N = a.horizon
+    scale = np.array([0.2, 0.5])
+    rng = np.random.default_rng(np.random.PCG64(SEED + 4242))
+    gaps = rng.exponential(1.0 / a.rate, size=int(a.rate * a.duration * 2) + 16)
+    arr = np.cumsum(gaps)
+    arr = arr[arr < a.duration]
+    n = arr.size
+    keys = np.column_stack([rng.uniform(-0.2, 0.2, n), rng.uniform(-0.5, 0.5, n)])
+    P, sd = relax_all(S, [wl.pendulum_problem(N=N, theta0=float(t), omega0=float(w)) for t, w in keys])
+    opts = dict(tol=1e-6, maxiter=a.maxiter, precision=S.STROM_PREC_MIXED, polish_eta=a.polish_eta,
+                check_every=a.step_iters)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    clk = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clk.start()
+    out = {}
+    for mode in ("cold", "warm"):
+        batch = S.Batch(sd[0], a.slots, **opts)
+        store = None
+        if mode == "warm":
+            store = S.WarmStore(2, sd[0].nsvec, n)
+            batch.set_warm(store, record=True)
+        pending = {}
+        lat, its, cert, ok = [], [], 0, 0
+        nxt = 0
+        drain = a.duration + 45.0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        while True:
+            now = time.perf_counter() - t0
+            while nxt < n and arr[nxt] <= now:
+                if mode == "warm":
+                    t = batch.submit_keyed(sd[nxt], keys[nxt] / scale, P[nxt])
+                else:
+                    t = batch.submit(sd[nxt], P[nxt])
+                pending[t] = nxt
+                nxt += 1
+            if not pending and nxt >= n:
+                break
+            if now > drain:
+                break
+            if pending:
+                batch.step(a.step_iters, sp)
+            else:
+                time.sleep(max(0.0, min(0.01, arr[nxt] - now)))
+            done_at = time.perf_counter() - t0
+            for t in list(pending):
+                o = batch.poll(t)
+                if o is None:
+                    continue
+                j = pending.pop(t)
+                res, c, _ = o
+                if res.status == S.STROM_OK:
+                    ok += 1
+                    lat.append(done_at - arr[j])
+                    its.append(res.iterations)
+                    cert += bool(c is not None and c.certified)
+        span = time.perf_counter() - t0
+        lat, its = np.array(lat or [np.nan]), np.array(its or [0])
+        out[mode] = {"arrived": int(n), "converged": ok, "certified": cert, "unfinished": len(pending),
+                     "solves_per_s": ok / span, "span_s": span,
+                     "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+                     "iterations_p50": float(np.percentile(its, 50)), "iterations_p99": float(np.percentile(its, 99)),
+                     "store_entries": len(store) if store is not None else 0}
+        del batch, store
+    clocks = clk.stop()
+    line = {"metric": "served pendulum requests under Poisson arrivals: latency (arrival to result) and solves/s",
+            "value": out["warm"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "higher_is_better": True, "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": "pendulum swing-up N=%d, (theta0, omega0) ~ U([-0.2,0.2] x [-0.5,0.5]) seeded, "
+                                   "Poisson arrivals %.0f/s for %.0f s (%d requests), %d slots, %d iterations per "
+                                   "serving step, KKT<=1e-6, certificate per request" %
+                                   (N, a.rate, a.duration, n, a.slots, a.step_iters),
+                       "warm": "each converged request is recorded (key = initial state); a new request starts "
+                               "from the combination of its nearest recorded solutions; store empty at start"},
+            "cold": out["cold"], "warm": out["warm"], "clocks": clocks}
+    print(json.dumps(line))
+
+
 def main():
     a = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -686,6 +783,8 @@ def main():
         run_psd(a)
     elif a.workload == "warm":
         run_warm(a)
+    elif a.workload == "poisson":
+        run_poisson(a)
     else:
         run_strom(a, rank, world)
 
