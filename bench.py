@@ -386,12 +386,20 @@ def roofline(S, solver, sdps, stream):
     torch.cuda.synchronize()
     t_psd = e0.elapsed_time(e1) / 1e3 / reps
     f_psd = psd_flops(ns.tolist())
-    fp64_peak = 1.208  # TFLOP/s, FMA-loop probe on this GPU (152 SMs x 2 FP64 FMA/clk)
-    fp32_peak = 75.49  # TFLOP/s, FMA-loop probe on this GPU (152 SMs x 128 FP32 FMA/clk)
+    # ALU peaks from unit counts and the maximum SM clock: 152 SMs x 2 FP64
+    # (128 FP32) FMA per clock x 2 flops x 2.07 GHz; an FMA-loop probe on
+    # this part measured 1.208 and 75.49 TFLOP/s
+    fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    # DRAM bytes (read + write) of one y-solve launch over 1024 pendulum
+    # (N = 10) instances, from an ncu capture of the unchanged kernel
+    traffic = 1.708e9 + 39.6e6 if (len(sdps) == 1024 and sdps[0].info.N == 10) else None
     if 2 * t_solve >= t_psd:
         ach = f_solve / t_solve / 1e12
-        return {"kernel": "chain_solve_kernel (block-banded y-solve, FP64)", "bound": "alu", "achieved": ach,
-                "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": None,
+        return {"kernel": "chain y-solve, FP64 (chain_solve_multi_kernel<2>: tiles of 2 instances sharing the "
+                          "factor of cliques 2..N)", "bound": "alu", "achieved": ach,
+                "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": traffic,
+                "peak_basis": "unit counts x 2.07 GHz (FMA-loop probe: 1.208 TFLOP/s FP64)",
                 "launch_ms": 1e3 * t_solve, "other": {"jacobi_psd_fp32_ms": 1e3 * t_psd,
                                                       "jacobi_psd_fp32_tflops": f_psd / t_psd / 1e12}}
     ach = f_psd / t_psd / 1e12
@@ -549,7 +557,7 @@ def run_psd(a):
         torch.cuda.synchronize()
     te = (time.perf_counter() - t0) / a.steps
     flops = psd_flops(n.tolist())
-    fp = 75.49 if a.precision == 1 else 1.208
+    fp = 152 * (128 if a.precision == 1 else 2) * 2 * 2.07e9 / 1e12   # unit counts x 2.07 GHz
     line = {"metric": "PSD projections per second (4096-block microbench)", "value": len(n) / t, "unit": "blocks/s",
             "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if a.precision == 1 else "f64",
