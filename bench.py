@@ -396,8 +396,9 @@ def roofline(S, solver, sdps, stream):
     traffic = 1.708e9 + 39.6e6 if (len(sdps) == 1024 and sdps[0].info.N == 10) else None
     if 2 * t_solve >= t_psd:
         ach = f_solve / t_solve / 1e12
-        return {"kernel": "chain y-solve, FP64 (chain_solve_multi_kernel<2>: tiles of 2 instances sharing the "
-                          "factor of cliques 2..N)", "bound": "alu", "achieved": ach,
+        kname = ("chain_solve_multi_kernel<2> (tiles of 2 instances sharing the factor of cliques 2..N)"
+                 if len(sdps) >= 304 else "chain_solve_kernel")
+        return {"kernel": "chain y-solve, FP64: " + kname, "bound": "alu", "achieved": ach,
                 "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": traffic,
                 "peak_basis": "unit counts x 2.07 GHz (FMA-loop probe: 1.208 TFLOP/s FP64)",
                 "launch_ms": 1e3 * t_solve, "other": {"jacobi_psd_fp32_ms": 1e3 * t_psd,
