@@ -196,6 +196,35 @@ def combine_ranks(dist, t, counts, device):
     return float(tt.item()), [int(round(c)) for c in cc.tolist()]
 
 
+def run_e2e(S, batch, feed, per_step, steps, iters, stream, outstanding, harvest, sync):
+    """Serving end to end through the public API: each step builds its
+    replacement requests from polynomial data (relaxation), submits them,
+    serves `iters` iterations and reads every finished result on the host.
+    The requests of step k + 1 are built on a host thread while the GPU
+    serves step k (the library calls release the interpreter lock).
+    Returns (counted solves, seconds, transfer bytes before, after, tickets
+    still outstanding)."""
+    from concurrent.futures import ThreadPoolExecutor
+    done = 0
+    with ThreadPoolExecutor(max_workers=1) as prep:
+        b0 = S.transfer_bytes()
+        t0 = time.perf_counter()
+        nxt = prep.submit(feed.take, per_step)
+        for _ in range(steps):
+            P, sd = nxt.result()
+            outstanding += [batch.submit(x, pr) for x, pr in zip(sd, P)]
+            del P, sd
+            nxt = prep.submit(feed.take, per_step)
+            batch.step(iters, stream)
+            d, outstanding = harvest(outstanding)
+            done += sum(1 for f in d if f[0].status == S.STROM_OK and f[1] is not None and f[1].xi == f[1].xi)
+        sync()
+        te = time.perf_counter() - t0
+        b1 = S.transfer_bytes()
+        del nxt   # requests prepared for a step that is not run
+    return done, te, b0, b1, outstanding
+
+
 def run_strom(a, rank, world):
     import numpy as np
     import torch
@@ -268,22 +297,9 @@ def run_strom(a, rank, world):
                 "xi_le_1pct": sum(f[1].xi <= 1e-2 for f in ok), "certified": sum(f[1].certified for f in ok),
                 "of": len(ok)}
 
-    # ---- end to end through the public API, continuing the same warmed batch:
-    # each step builds its replacement requests from polynomial data
-    # (relaxation), submits them, serves, and reads the results on the host
-    h2d0, d2h0 = S.transfer_bytes()
-    te0 = time.perf_counter()
-    e2e_done = 0
-    for _ in range(a.steps):
-        P, sd = feed.take(per_step)
-        outstanding += [batch.submit(x, pr) for x, pr in zip(sd, P)]
-        del P, sd
-        batch.step(it, sp)
-        d, outstanding = harvest(outstanding)
-        e2e_done += sum(1 for f in d if f[0].status == S.STROM_OK and f[1] is not None and f[1].xi == f[1].xi)
-    torch.cuda.synchronize()
-    te = time.perf_counter() - te0
-    h2d1, d2h1 = S.transfer_bytes()
+    # ---- end to end through the public API, continuing the same warmed batch
+    e2e_done, te, (h2d0, d2h0), (h2d1, d2h1), outstanding = run_e2e(
+        S, batch, feed, per_step, a.steps, it, sp, outstanding, harvest, torch.cuda.synchronize)
     e2e = {"value": e2e_done / te, "unit": "solves/s", "h2d_bytes_per_step": (h2d1 - h2d0) // a.steps,
            "d2h_bytes_per_step": (d2h1 - d2h0) // a.steps}
     del batch
