@@ -98,6 +98,9 @@ int strom::warm_append(strom_warm* w, const double* key, const double* X_dev, co
   double* dst = w->XS.p + (int64_t)w->n * 2 * w->nsvec;
   STROM_CUDA(cudaMemcpyAsync(dst, X_dev, sizeof(double) * w->nsvec, cudaMemcpyDeviceToDevice, st));
   STROM_CUDA(cudaMemcpyAsync(dst + w->nsvec, S_dev, sizeof(double) * w->nsvec, cudaMemcpyDeviceToDevice, st));
+  // the entry is complete before any other stream (strom_warm_get, another
+  // solver's warm start) can read it
+  STROM_CUDA(cudaStreamSynchronize(st));
   w->keys.insert(w->keys.end(), key, key + w->d);
   w->sigma.push_back(sigma);
   return w->n++;
