@@ -235,13 +235,18 @@ class Solver:
         return n.value
 
     def reset(self, i=-1, X0=None, S0=None, sigma=0.0):
+        if i >= 0:
+            _check_len(X0, self.sdps[i].nsvec, "X0")
+            _check_len(S0, self.sdps[i].nsvec, "S0")
+        elif X0 is not None or S0 is not None:
+            raise ValueError("X0 / S0 need one instance (i >= 0)")
         px = None if X0 is None else _ptr(np.ascontiguousarray(X0, np.float64), C.c_double)
         ps = None if S0 is None else _ptr(np.ascontiguousarray(S0, np.float64), C.c_double)
         check(lib().strom_solver_reset(self.handle, i, px, ps, float(sigma)), "strom_solver_reset")
 
     def warm_start(self, i, store: WarmStore, key):
         """Reset instance i to the store's warm start for key (cold when the store is empty)."""
-        _, pk = _key(key)
+        _, pk = _key(key, store.key_dim)
         check(lib().strom_solver_warm_start(self.handle, i, store.handle, pk), "strom_solver_warm_start")
 
     def result(self, i=0) -> Result:
@@ -301,8 +306,16 @@ class Solver:
         check(lib().strom_kernel_solve(self.handle, r_ptr, y_ptr, stream), "strom_kernel_solve")
 
 
-def _key(key):
-    k = np.ascontiguousarray(np.atleast_1d(np.asarray(key, np.float64)))
+def _check_len(a, n, name):
+    if a is not None and np.asarray(a).size != n:
+        raise ValueError("%s must have %d entries" % (name, n))
+
+
+def _key(key, dim=None):
+    """A key as a contiguous float64 array (checked against the store's key dimension)."""
+    k = np.ascontiguousarray(np.atleast_1d(np.asarray(key, np.float64)).ravel())
+    if dim is not None and k.size != dim:
+        raise ValueError("warm-start key has %d entries, the store's keys have %d" % (k.size, dim))
     return k, _ptr(k, C.c_double)
 
 
@@ -339,23 +352,25 @@ class WarmStore:
         return lib().strom_warm_count(self.handle)
 
     def add(self, key, X, S, sigma) -> int:
-        _, pk = _key(key)
-        X = np.ascontiguousarray(X, np.float64)
-        S = np.ascontiguousarray(S, np.float64)
+        _, pk = _key(key, self.key_dim)
+        X = np.ascontiguousarray(X, np.float64).ravel()
+        S = np.ascontiguousarray(S, np.float64).ravel()
+        if X.size != self.nsvec or S.size != self.nsvec:
+            raise ValueError("X and S must have nsvec = %d entries" % self.nsvec)
         j = C.c_int32()
         check(lib().strom_warm_add(self.handle, pk, _ptr(X, C.c_double), _ptr(S, C.c_double), float(sigma),
                                    C.byref(j)), "strom_warm_add")
         return j.value
 
     def add_from_solver(self, solver: "Solver", i: int, key) -> int:
-        _, pk = _key(key)
+        _, pk = _key(key, self.key_dim)
         j = C.c_int32()
         check(lib().strom_warm_add_from_solver(self.handle, solver.handle, i, pk, C.byref(j)),
               "strom_warm_add_from_solver")
         return j.value
 
     def query(self, key):
-        _, pk = _key(key)
+        _, pk = _key(key, self.key_dim)
         idx, wt, n = np.zeros(self.key_dim + 1, np.int32), np.zeros(self.key_dim + 1), C.c_int32()
         check(lib().strom_warm_query(self.handle, pk, _ptr(idx, C.c_int32), _ptr(wt, C.c_double), C.byref(n)),
               "strom_warm_query")
@@ -384,6 +399,8 @@ class Batch:
             self.handle = None
 
     def submit(self, sdp: Sdp, problem: Problem | None = None, X0=None, S0=None) -> int:
+        _check_len(X0, sdp.nsvec, "X0")
+        _check_len(S0, sdp.nsvec, "S0")
         t = C.c_uint64()
         px = None if X0 is None else _ptr(np.ascontiguousarray(X0, np.float64), C.c_double)
         ps = None if S0 is None else _ptr(np.ascontiguousarray(S0, np.float64), C.c_double)
@@ -398,7 +415,8 @@ class Batch:
 
     def submit_keyed(self, sdp: Sdp, key, problem: Problem | None = None) -> int:
         t = C.c_uint64()
-        _, pk = _key(key)
+        store = getattr(self, "warm", None)
+        _, pk = _key(key, store.key_dim if store is not None else None)
         check(lib().strom_batch_submit_keyed(self.handle, sdp.handle, problem.handle if problem else None, pk,
                                              C.byref(t)), "strom_batch_submit_keyed")
         return t.value

@@ -75,3 +75,16 @@ def test_no_gpu_no_fallback(S):
     sdp = S.Problem(wl.toy_problem(N=2)).relax()
     with pytest.raises(RuntimeError):
         S.Solver([sdp])
+
+
+def test_binding_checks_array_lengths(S):
+    """The binding rejects keys and warm states whose length does not match
+    before the library would read past them."""
+    from paper_2406_05846_gb300 import api
+    api._key([0.1, 0.2], 2)
+    with pytest.raises(ValueError, match="key"):
+        api._key([0.1, 0.2, 0.3], 2)
+    api._check_len(None, 5, "X0")
+    api._check_len(np.zeros(5), 5, "X0")
+    with pytest.raises(ValueError, match="X0"):
+        api._check_len(np.zeros(4), 5, "X0")
