@@ -33,10 +33,12 @@ def test_exports_every_declared_symbol(S):
     assert names == set(_native.SIGNATURES), names ^ set(_native.SIGNATURES)
 
 
-@pytest.mark.parametrize("which", ["toy", "pendulum", "cartpole", "rigid"])
+@pytest.mark.parametrize("which", ["toy", "pendulum", "paper_pendulum", "cartpole", "rigid"])
 def test_builder_matches_oracle(S, which):
     if which == "toy":
         p = wl.toy_problem(N=3)
+    elif which == "paper_pendulum":
+        p = wl.paper_pendulum_problem(N=3, theta0=0.4, thetadot0=-0.5)
     elif which == "pendulum":
         p = wl.pendulum_problem(N=5, theta0=0.13)
     elif which == "cartpole":
@@ -88,3 +90,16 @@ def test_binding_checks_array_lengths(S):
     api._check_len(np.zeros(5), 5, "X0")
     with pytest.raises(ValueError, match="X0"):
         api._check_len(np.zeros(4), 5, "X0")
+
+
+def test_builder_reproduces_paper_pendulum_sizes(S):
+    """Table 1's pendulum row and the sizes quoted in Sec. 1, from the C++ builder."""
+    import test_oracle_relax as T
+    want = T._paper_sizes()
+    sd = S.Problem(wl.paper_pendulum_problem(N=30, theta0=0.4, thetadot0=-0.5)).relax()
+    a = sd.export()
+    assert int(np.sum(a.block_kind == 0)) == want["nM"][0]
+    assert set(a.block_n[a.block_kind == 0].tolist()) == {want["sizeM"][0]}
+    assert int(np.sum(a.block_kind == 1)) == want["nL"][0]
+    assert set(a.block_n[a.block_kind == 1].tolist()) == {want["sizeL"][0]}
+    assert sd.m == want["m"][0] and sd.nsvec == want["nvar"][0]

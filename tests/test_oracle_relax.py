@@ -212,3 +212,63 @@ def test_pendulum_shapes():
     sizes = [b.n for b in sdp.blocks]
     assert sizes.count(36) == 10 and sizes.count(8) == 20
     assert sdp.nsvec == 10 * 666 + 20 * 36
+
+
+# --------------------------------------------------------------------------
+# the paper's own pendulum model reproduces the printed SDP sizes
+# --------------------------------------------------------------------------
+def _paper_sizes():
+    out = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "paper_pendulum_sizes.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, v, cite = (x.strip() for x in line.split("|"))
+            out[k] = (int(v), cite)
+    return out
+
+
+def test_paper_pendulum_sizes():
+    sdp = R.relax(wl.paper_pendulum_problem(N=30, theta0=0.4, thetadot0=-0.5))
+    want = _paper_sizes()
+    M = [b for b in sdp.blocks if b.kind == "M"]
+    L = [b for b in sdp.blocks if b.kind == "L"]
+    assert len(M) == want["nM"][0], want["nM"][1]
+    assert {b.n for b in M} == {want["sizeM"][0]}, want["sizeM"][1]
+    assert len(L) == want["nL"][0], want["nL"][1]
+    assert {b.n for b in L} == {want["sizeL"][0]}, want["sizeL"][1]
+    assert sdp.m == want["m"][0], want["m"][1]
+    assert sdp.nsvec == want["nvar"][0], want["nvar"][1]
+
+
+def _paper_pend_rollout(p, U):
+    """Explicit simulation of the paper's pendulum (rate update, then the
+    rotation by the previous step's increment), rescaled control U = u / u_max."""
+    m = p.meta
+    dt, umax = m["dt"], m["u_max"]
+    ml2, mgl, b = 1.0, 9.8, 0.1                     # m = l = 1, g = 9.8, b = 0.1 (the defaults)
+    rc, rs = np.cos(m["theta0"]), np.sin(m["theta0"])
+    fc, fs = np.cos(dt * m["thetadot0"]), np.sin(dt * m["thetadot0"])
+    z = [rc, rs, fc, fs]
+    for Uk in U:
+        fs_n = fs + dt * dt / ml2 * (umax * Uk - mgl * rs - b * fs / dt)
+        fc_n = np.sqrt(1.0 - fs_n * fs_n)
+        rc_n, rs_n = rc * fc - rs * fs, rs * fc + rc * fs
+        z += [Uk, rc_n, rs_n, fc_n, fs_n]
+        rc, rs, fc, fs = rc_n, rs_n, fc_n, fs_n
+    return np.array(z)
+
+
+def test_paper_pendulum_lifting_feasible():
+    # a rollout of the paper's dynamics satisfies every row exactly when
+    # lifted to rank-1 moment matrices, and <C, X> is its cost
+    rng = np.random.default_rng(4)
+    p = wl.paper_pendulum_problem(N=5, theta0=0.3, thetadot0=0.7)
+    z = _paper_pend_rollout(p, rng.uniform(-1, 1, 5))
+    sdp = R.relax(p)
+    X = R.lift_rank1(p, sdp, z)
+    assert np.max(np.abs(sdp.A @ X - sdp.b)) < 1e-12
+    assert abs(sdp.C @ X - p.objective(z)) < 1e-12 * (1 + abs(p.objective(z)))
+    for k, c in enumerate(p.cliques):                 # the bounds hold along the rollout
+        zk = p.clique_vars(z, k)
+        assert all(g.evaluate(zk) >= -1e-12 for g in c.g)
+    z[5] += 1e-3                                      # break r_c of x_1
+    assert np.max(np.abs(sdp.A @ R.lift_rank1(p, sdp, z) - sdp.b)) > 1e-5

@@ -7,10 +7,10 @@ It contains none of the relaxation, ADMM or projection arithmetic; both the
 oracle and the CUDA path read what it produces.
 """
 from .poly import Poly
-from .problems import (Problem, Clique, toy_problem, pendulum_problem,
+from .problems import (Problem, Clique, toy_problem, pendulum_problem, paper_pendulum_problem,
                        cartpole_problem, rigid_body_problem, problem_batch)
 from .psd_bench import psd_microbench, known_spectrum_blocks
 
-__all__ = ["Poly", "Problem", "Clique", "toy_problem", "pendulum_problem",
+__all__ = ["Poly", "Problem", "Clique", "toy_problem", "pendulum_problem", "paper_pendulum_problem",
            "cartpole_problem", "rigid_body_problem", "problem_batch",
            "psd_microbench", "known_spectrum_blocks"]

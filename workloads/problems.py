@@ -138,6 +138,60 @@ def pendulum_problem(N: int = 10, dt: float = 0.1, theta0: float = 0.1, g_l: flo
 
 
 # --------------------------------------------------------------------------
+# the paper's pendulum (App. "Inverted Pendulum"): Lie-group variational
+# integrator on SO(2), state x = (r_c, r_s, f_c, f_s), control u
+# --------------------------------------------------------------------------
+def paper_pendulum_problem(N: int = 30, dt: float = 0.1, theta0: float = 0.0, thetadot0: float = 0.0,
+                           m: float = 1.0, l: float = 1.0, b: float = 0.1, g: float = 9.8,
+                           fc_min: float = 0.5, u_max: float = 5.0, Pf: float = 1.0) -> Problem:
+    """The inverted pendulum of the paper's experiments, 9-variable cliques.
+
+    r = (r_c, r_s) is the attitude (cos, sin of theta) and f = (f_c, f_s) the
+    rotation from one step to the next (f_s / dt ~ the angular rate). Per
+    clique k, with u scaled to U = u / u_max:
+      rate     : m l^2 (f_s,k - f_s,k-1) / dt^2 = u_{k-1} - m g l r_s,k-1 - b f_s,k-1 / dt
+      rotation : r_c,k = r_c,k-1 f_c,k-1 - r_s,k-1 f_s,k-1,
+                 r_s,k = r_s,k-1 f_c,k-1 + r_c,k-1 f_s,k-1
+      SO(2)    : r_c^2 + r_s^2 = 1 and f_c^2 + f_s^2 = 1 for x_k, and for
+                 x_{k-1} when k >= 2 (x_0 is fixed by the initial condition)
+      bounds   : f_c,k - fc_min >= 0, 1 - U_{k-1}^2 >= 0 (two localizing blocks)
+      initial  : x_0 = (cos theta0, sin theta0, cos(dt thetadot0), sin(dt thetadot0))
+      cost     : the LQR-style loss to x_f = (-1, 0, 1, 0) (theta = pi, at rest)
+                 with identity weights, Pf on x_N.
+    With N = 30 this has the sizes of the paper's pendulum row of Table 1:
+    30 moment blocks 55 x 55, 60 localizing blocks 10 x 10, 47,351 rows and
+    49,500 svec entries.
+    """
+    nv = 9
+    v = [Poly.var(nv, i) for i in range(nv)]
+    rc0, rs0, fc0, fs0, U, rc1, rs1, fc1, fs1 = v
+    xf = (-1.0, 0.0, 1.0, 0.0)
+    x_prev, x_next = (rc0, rs0, fc0, fs0), (rc1, rs1, fc1, fs1)
+    raw = []
+    for k in range(1, N + 1):
+        f = sum((xi - t) * (xi - t) for xi, t in zip(x_prev, xf)) + U * U
+        if k == N:
+            f = f + Pf * sum((xi - t) * (xi - t) for xi, t in zip(x_next, xf))
+        h = [m * l * l / (dt * dt) * (fs1 - fs0) - u_max * U + m * g * l * rs0 + b / dt * fs0,
+             rc1 - rc0 * fc0 + rs0 * fs0,
+             rs1 - rs0 * fc0 - rc0 * fs0,
+             rc1 * rc1 + rs1 * rs1 - 1.0,
+             fc1 * fc1 + fs1 * fs1 - 1.0]
+        if k >= 2:
+            h += [rc0 * rc0 + rs0 * rs0 - 1.0, fc0 * fc0 + fs0 * fs0 - 1.0]
+        else:
+            h += [rc0 - np.cos(theta0), rs0 - np.sin(theta0), fc0 - np.cos(dt * thetadot0),
+                  fs0 - np.sin(dt * thetadot0)]
+        gg = [fc1 - fc_min, 1.0 - U * U]
+        raw.append((f, gg, h))
+    fscale = 1.0 / max(f.max_abs_coef() for f, _, _ in raw)
+    cl = [Clique(f * fscale, [p.normalized() for p in gg], [p.normalized() for p in h]) for f, gg, h in raw]
+    return Problem("paper_pendulum", N, 4, 1, cl, R=1.0,
+                   meta=dict(dt=dt, theta0=theta0, thetadot0=thetadot0, u_max=u_max, fc_min=fc_min,
+                             fscale=fscale))
+
+
+# --------------------------------------------------------------------------
 # cart-pole swing-up: state (x, v, c, s, w), control force f
 # --------------------------------------------------------------------------
 def cartpole_problem(N: int = 50, dt: float = 0.05, x0: float = 0.0, theta0: float = 0.0,
