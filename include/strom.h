@@ -268,6 +268,31 @@ uint64_t strom_launch_count(void);
 void strom_transfer_bytes(uint64_t* h2d, uint64_t* d2h);
 
 /* ------------------------------------------------------------------------
+ * Rank tests of one moment matrix beyond the rank-1 test (host only).
+ * M: the n x n moment matrix of order 2 in nv clique variables (basis [z]_2
+ * in graded lexicographic order, n = (nv + 1)(nv + 2) / 2), column-major,
+ * e.g. from strom_get_moment. Numerical ranks count eigenvalues above
+ * tol * lambda_max.
+ *   rank, rank_low: of M and of its principal submatrix on [z]_1 (degree
+ *     <= 1); flat = (rank == rank_low), the flat-extension condition that
+ *     generalises rank 1 (Sec. 2.2): the moments then come from a measure
+ *     with exactly `rank` atoms.
+ *   ratio_sub: lambda_2 / lambda_1 of the principal submatrix on the
+ *     monomials of the variables selected by vars (nv flags; NULL = all),
+ *     the partial rank-1 test of the car back-in experiment, whose auxiliary
+ *     variables keep M_k above rank 1 while the trajectory's submatrix is
+ *     rank 1; zbar (nullable, [nv]) receives the degree-1 entries of that
+ *     submatrix's top eigenvector scaled to a leading 1 (NaN for variables
+ *     not selected).
+ * Errors: INVALID (bad sizes, non-finite or non-symmetric M). */
+typedef struct {
+  int32_t n, rank, rank_low, flat, n_sub;
+  double ratio_sub, lambda_max;
+} strom_rank_test;
+int strom_moment_rank_test(const double* M, int32_t nv, const uint8_t* vars, double tol, strom_rank_test* out,
+                           double* zbar);
+
+/* ------------------------------------------------------------------------
  * Serving by continuous batching. A batch owns `slots` solver slots for
  * SDPs with the structure of `tmpl` (same horizon, blocks, rows and sparsity
  * pattern; values of A, b and C may differ, as they do between initial

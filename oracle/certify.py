@@ -143,3 +143,47 @@ def certify(problem, red, X, y, rank_tol=1e-4, xi_tol=1e-2, feas_tol=1e-9) -> Ce
     rank_one = mr <= rank_tol
     return Certificate(ratios, mr, zbar, zhat, hmax, gmin, feasible, phat, lb, xi, rank_one,
                        bool(rank_one and feasible and xi <= xi_tol))
+
+
+# --------------------------------------------------------------------------
+# flat extension and partial rank-1 tests of one moment matrix (Sec. 2.2:
+# the flat-extension condition generalises rank 1; App. car back-in: the
+# submatrix of the trajectory variables can be rank-1 when M_k is not)
+# --------------------------------------------------------------------------
+def _numerical_rank(W, tol):
+    top = max(W[-1], 0.0)
+    return int(np.sum(W > tol * top)) if top > 0 else 0
+
+
+def moment_rank_tests(M, nv: int, vars_mask=None, tol: float = 1e-8):
+    """Rank tests of a moment matrix M of order 2 in nv variables (basis [z]_2,
+    graded lexicographic order).
+
+    rank      numerical rank of M (eigenvalues above tol * lambda_max)
+    rank_low  the same for the principal submatrix on [z]_1 (degree <= 1)
+    flat      rank == rank_low (flat extension: the moments come from a
+              measure with exactly rank atoms)
+    ratio_sub lambda_2 / lambda_1 of the principal submatrix on the monomials
+              whose variables all lie in vars_mask (all variables if None)
+    zbar_sub  its top eigenvector scaled to a leading 1, entries of the
+              degree-1 monomials of the selected variables (NaN elsewhere)
+    """
+    from .relax import monomial_basis
+    basis = monomial_basis(nv, 2)
+    M = np.asarray(M, dtype=np.float64)
+    sel = np.ones(nv, bool) if vars_mask is None else np.asarray(vars_mask, bool)
+    W = np.linalg.eigvalsh(M)
+    low = [i for i, e in enumerate(basis) if sum(e) <= 1]
+    W_low = np.linalg.eigvalsh(M[np.ix_(low, low)])
+    sub = [i for i, e in enumerate(basis) if all(sel[t] or e[t] == 0 for t in range(nv))]
+    Ws, Qs = np.linalg.eigh(M[np.ix_(sub, sub)])
+    ratio = Ws[-2] / Ws[-1] if (len(sub) > 1 and Ws[-1] > 0) else (0.0 if Ws[-1] > 0 else np.inf)
+    v = Qs[:, -1] / Qs[0, -1]
+    zbar = np.full(nv, np.nan)
+    for j, i in enumerate(sub):
+        e = basis[i]
+        if sum(e) == 1:
+            zbar[e.index(1)] = v[j]
+    rank, rank_low = _numerical_rank(W, tol), _numerical_rank(W_low, tol)
+    return dict(n=len(basis), rank=rank, rank_low=rank_low, flat=rank == rank_low, n_sub=len(sub),
+                ratio_sub=float(ratio), lambda_max=float(W[-1]), zbar_sub=zbar)

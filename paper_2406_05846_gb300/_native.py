@@ -61,6 +61,11 @@ class strom_certificate(C.Structure):
                 ("certified", C.c_int32)]
 
 
+class strom_rank_test(C.Structure):
+    _fields_ = [("n", C.c_int32), ("rank", C.c_int32), ("rank_low", C.c_int32), ("flat", C.c_int32),
+                ("n_sub", C.c_int32), ("ratio_sub", C.c_double), ("lambda_max", C.c_double)]
+
+
 P = C.c_void_p
 PD = C.POINTER(C.c_double)
 PI32 = C.POINTER(C.c_int32)
@@ -87,6 +92,7 @@ SIGNATURES = {
     "strom_solve": (C.c_int, [P, P]),
     "strom_solver_factor": (C.c_int, [P, P]),
     "strom_certify_batch": (C.c_int, [P, C.POINTER(P), C.c_double, C.c_double, C.POINTER(strom_certificate)]),
+    "strom_moment_rank_test": (C.c_int, [PD, C.c_int32, PU8, C.c_double, C.POINTER(strom_rank_test), PD]),
     "strom_launch_count": (C.c_uint64, []),
     "strom_transfer_bytes": (None, [C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
     "strom_solver_step": (C.c_int, [P, C.c_int32, P, PI32]),

@@ -464,6 +464,23 @@ class PsdPlan:
         check(lib().strom_psd_execute(self.handle, xb_ptr, out_ptr, lam_ptr, stream), "strom_psd_execute")
 
 
+def moment_rank_test(M, nv: int, vars_mask=None, tol: float = 1e-8):
+    """strom_moment_rank_test: flat-extension and partial rank-1 tests of one moment matrix."""
+    M = np.asfortranarray(np.asarray(M, np.float64))
+    n = (nv + 1) * (nv + 2) // 2
+    if M.shape != (n, n):
+        raise ValueError("M must be %d x %d for nv = %d" % (n, n, nv))
+    vm = None if vars_mask is None else np.ascontiguousarray(np.asarray(vars_mask, bool).astype(np.uint8))
+    if vm is not None and vm.size != nv:
+        raise ValueError("vars_mask must have nv entries")
+    out, z = N.strom_rank_test(), np.empty(nv)
+    check(lib().strom_moment_rank_test(M.ctypes.data_as(C.POINTER(C.c_double)), nv,
+                                       None if vm is None else _ptr(vm, C.c_uint8), float(tol), C.byref(out),
+                                       _ptr(z, C.c_double)), "strom_moment_rank_test")
+    return dict(n=out.n, rank=out.rank, rank_low=out.rank_low, flat=bool(out.flat), n_sub=out.n_sub,
+                ratio_sub=out.ratio_sub, lambda_max=out.lambda_max, zbar_sub=z)
+
+
 def launch_count() -> int:
     """Kernels launched by libstrom in this process (graph nodes counted per replay)."""
     return int(lib().strom_launch_count())
