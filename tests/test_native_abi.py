@@ -103,3 +103,32 @@ def test_builder_reproduces_paper_pendulum_sizes(S):
     assert int(np.sum(a.block_kind == 1)) == want["nL"][0]
     assert set(a.block_n[a.block_kind == 1].tolist()) == {want["sizeL"][0]}
     assert sd.m == want["m"][0] and sd.nsvec == want["nvar"][0]
+
+
+def test_plain_c_client(S, tmp_path):
+    """A C program uses the library through include/strom.h alone (no Python):
+    the toy problem built there relaxes to the same SDP as through the
+    binding, and the host-only calls give the expected results."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    libdir = os.path.join(ROOT, "paper_2406_05846_gb300")
+    exe = str(tmp_path / "c_client")
+    subprocess.run([cc, "-std=c99", "-O1", "-Wall", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "c_client.c"), "-L", libdir, "-lstrom", "-lm",
+                    "-Wl,-rpath," + libdir, "-o", exe], check=True)
+    out = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stdout + out.stderr
+    lines = dict(l.split(" ", 1) for l in out.stdout.strip().splitlines())
+    info = S.Problem(wl.toy_problem(N=3)).relax().info
+    assert lines["problem_create"] == "0" and lines["relax"] == "0"
+    want = "nblocks %d nsvec %d m %d nnz %d kinds %s" % (info.nblocks, info.nsvec, info.m, info.nnz,
+                                                         " ".join(str(x) for x in info.rows_by_kind))
+    assert lines["info"] == want
+    assert lines["export"] == "0 import 0 same 1"
+    assert lines["bad_import"] == "-1"
+    assert lines["warm_select"] == "0 k 3 idx 0 2 1 wt 0.500000 0.300000 0.200000"
+    assert lines["rank_test"] == "0 rank 1 flat 1 zbar 0.500000 -0.250000 0.750000"
+    assert lines["solver_create"] in ("ok", "cuda-unavailable")
