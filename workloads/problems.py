@@ -296,7 +296,10 @@ def problem_batch(kind: str, B: int, seed: int = BASE_SEED, **kw):
             out.append(cartpole_problem(x0=float(rng.uniform(-0.5, 0.5)),
                                         theta0=float(rng.uniform(-0.3, 0.3)), **kw))
         elif kind == "rigid_body":
-            N = kw.pop("N", None) or int(rng.integers(20, 101))
+            # a horizon given by the caller holds for every instance; otherwise
+            # each instance draws its own N ~ U{20..100}
+            rest = {k: v for k, v in kw.items() if k != "N"}
+            N = kw.get("N") or int(rng.integers(20, 101))
             nd = int(rng.integers(2, 5))
             start = (-1.5, -1.5, 0.0)
             goal = (float(rng.uniform(-1, 1)), float(rng.uniform(-1, 1)), float(rng.uniform(-np.pi, np.pi)))
@@ -307,7 +310,7 @@ def problem_batch(kind: str, B: int, seed: int = BASE_SEED, **kw):
                 if (np.hypot(ox - start[0], oy - start[1]) > rho + 0.2
                         and np.hypot(ox - goal[0], oy - goal[1]) > rho + 0.2):
                     disks.append((float(ox), float(oy), float(rho)))
-            out.append(rigid_body_problem(N=N, start=start, goal=goal, disks=disks, **kw))
+            out.append(rigid_body_problem(N=N, start=start, goal=goal, disks=disks, **rest))
         else:
             raise ValueError(kind)
     return out
