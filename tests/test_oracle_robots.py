@@ -186,3 +186,47 @@ def test_rigid_body_batch_recipe():
     # same seed, same instances
     again = wl.problem_batch("rigid_body", 12, seed=5)
     assert [p.meta["goal"] for p in again] == [p.meta["goal"] for p in batch]
+
+
+def _cartpole_brute(p, x0, theta0):
+    """min over (F_0, F_1) in [-1, 1]^2 of the rollout cost, boxes enforced:
+    a 201 x 201 grid, then a bounded quasi-Newton refinement from its best point."""
+    import scipy.optimize as so
+
+    def cost(F):
+        F = np.clip(F, -1, 1)
+        z = cartpole_rollout(F, x0, theta0, **CP)
+        for k in range(1, p.N + 1):
+            xk = z[k * 6:k * 6 + 5]
+            if max(abs(xk[0]), abs(xk[1]), abs(xk[4])) > 1.0:
+                return np.inf
+        return p.objective(z)
+    g = np.linspace(-1, 1, 201)
+    best, F0 = np.inf, None
+    for a in g:
+        for b in g:
+            v = cost([a, b])
+            if v < best:
+                best, F0 = v, np.array([a, b])
+    r = so.minimize(cost, F0, bounds=[(-1, 1)] * 2, method="L-BFGS-B", options=dict(ftol=1e-15, gtol=1e-12))
+    return min(r.fun, best)
+
+
+def test_cartpole_relaxation_matches_brute_force():
+    """Theorem 1 on the cart-pole at N = 2: p*_kappa <= p* always, and with rank-1
+    moment matrices the relaxation is tight, so the oracle's sGS-ADMM optimum
+    equals a brute-force search of the nonconvex problem."""
+    from oracle import certify as CE
+    from oracle import sgs_admm as O
+    x0, th0 = 0.2, 0.15
+    p = _cartpole(2, x0=x0, theta0=th0)
+    pbf = _cartpole_brute(p, x0, th0)
+    red = O.reduce(R.relax(p))
+    res = O.solve(red, O.Options(tol=1e-9, maxiter=40000))
+    assert res.converged
+    cert = CE.certify(p, red, res.X, res.y)
+    assert res.pobj <= pbf + 1e-6 * (1 + abs(pbf))
+    assert cert.lower_bound <= pbf + 1e-9
+    assert cert.rank_one and cert.feasible
+    assert abs(res.pobj - pbf) <= 1e-6 * (1 + abs(pbf))
+    assert cert.phat >= pbf - 1e-9 * (1 + abs(pbf))
