@@ -10,6 +10,9 @@ Contents, each following the paper directly:
   sgs_admm   Algorithm 1 (sGS-ADMM) with the stopping rule of
              eq. (kkt-residual); PSD projection Pi(X) = Q max(0, W) Q^T
              (Sec. 4, parallel PSD cone projection)
+  jacobi     the same projection with a LAPACK-free cyclic-by-row Jacobi
+             eigensolver (Golub & Van Loan, Sec. 8.5), the reference of the
+             PSD-projection microbench
   certify    rank-1 test (Theorem 1 iii), extraction heuristic (Sec. 2.2),
              valid lower bound (eq. valid-lowerbound), suboptimality gap
              (eq. suboptimality-gap), R_beta (Theorem of App. C)

@@ -54,3 +54,48 @@ def test_svec_roundtrip_and_blocks():
     x = np.concatenate([v, R.svec(-M)])
     out = O.project_psd(x, [(0, n), (len(v), n)])
     assert np.allclose(out[:len(v)] - out[len(v):], v, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# the LAPACK-free cyclic Jacobi projection (Golub & Van Loan, Sec. 8.5)
+# --------------------------------------------------------------------------
+from oracle import jacobi as J  # noqa: E402
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 8, 17, 36])
+def test_jacobi_known_spectrum(n):
+    mats, lams, Qs = wl.known_spectrum_blocks([n, n], seed=12)
+    for A, lam, Q in zip(mats, lams, Qs):
+        w, V, sweeps = J.eig_jacobi(A)
+        scale = max(1.0, np.max(np.abs(lam)))
+        assert np.max(np.abs(np.sort(w) - np.sort(lam))) <= 1e-13 * scale
+        assert np.max(np.abs(V.T @ V - np.eye(n))) <= 1e-13 * n
+        assert np.max(np.abs((V * w) @ V.T - A)) <= 1e-13 * scale
+        want = (Q * np.maximum(lam, 0.0)) @ Q.T
+        assert np.max(np.abs(J.project_block(A) - want)) <= 1e-12 * scale
+        assert sweeps <= 12
+
+
+def test_jacobi_two_by_two_is_one_rotation():
+    # a single Schur rotation diagonalises a 2 x 2 block exactly (closed form)
+    a, b, c = 1.0, 2.0, -1.0
+    A = np.array([[a, b], [b, c]])
+    w, V, sweeps = J.eig_jacobi(A)
+    lp, lm = 0.5 * (a + c) + np.hypot(0.5 * (a - c), b), 0.5 * (a + c) - np.hypot(0.5 * (a - c), b)
+    assert sweeps <= 2                                                   # the second only sees rounding
+    assert np.allclose(np.sort(w), [lm, lp], atol=1e-15, rtol=0)
+    cs, sn = J.sym_schur2(A, 0, 1)
+    assert abs(cs * cs + sn * sn - 1.0) <= 4e-16
+    Jr = np.array([[cs, sn], [-sn, cs]])
+    B = Jr.T @ A @ Jr
+    assert abs(B[0, 1]) < 1e-15 and abs(B[1, 0]) < 1e-15
+    assert J.eig_jacobi(np.diag([3.0, -1.0]))[2] == 0                  # already diagonal: no sweep
+
+
+def test_jacobi_matches_the_eigh_projection_on_the_microbench_sizes():
+    """Every block size of the 4096-block microbench, including the two large
+    classes, projected by both oracle eigensolvers."""
+    mats, _, _ = wl.known_spectrum_blocks([8, 36, 78, 136], seed=13)
+    for A in mats:
+        P1, P2 = J.project_block(A), O.project_block(A)
+        assert np.max(np.abs(P1 - P2)) <= 1e-12 * np.max(np.abs(A))
