@@ -178,7 +178,10 @@ typedef struct {
                                 instance meeting tol in FP32 switches too, and it retires only
                                 on an FP64 iterate with eta <= tol */
   int32_t check_every;       /* host checks for completion every this many iterations */
-  double time_budget_s;      /* <= 0: none */
+  double time_budget_s;      /* strom_solve only: wall-clock budget in seconds, checked every
+                                check_every iterations; when spent, strom_solve returns
+                                STROM_ERR_TIMEOUT with the state and results of the last
+                                iteration run (valid, like MAXITER). <= 0: none */
   int32_t eig_warm_period;   /* FP32 eigensolver: start each block's sweeps from its eigenvectors of
                                 the previous iteration, restarting cold every this many iterations
                                 (0 = always cold); blocks of size <= 80 */
@@ -215,7 +218,9 @@ int32_t strom_solver_count(const strom_solver* s);
 int strom_solver_factor(strom_solver* s, void* stream);
 
 /* Runs Algorithm 1 until every instance meets tol or maxiter. Returns
- * STROM_OK when all converged, STROM_MAXITER otherwise. */
+ * STROM_OK when all converged, STROM_MAXITER otherwise, STROM_ERR_TIMEOUT
+ * when opt.time_budget_s ran out first, STROM_ERR_NUMERICAL when an
+ * instance met NaN / Inf. */
 int strom_solve(strom_solver* s, void* stream);
 /* Runs at most `iters` more iterations (instances that already met tol stay
  * frozen). *n_active receives the number of unconverged instances. */

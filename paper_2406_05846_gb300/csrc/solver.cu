@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -756,8 +757,25 @@ extern "C" int strom_solver_factor(strom_solver* s, void* stream) {
 
 extern "C" int strom_solve(strom_solver* s, void* stream) {
   int32_t act = 1;
-  int st = strom_solver_step(s, s ? s->opt.maxiter : 0, stream, &act);
-  if (st != STROM_OK) return st;
+  bool out_of_time = false;
+  if (s && s->opt.time_budget_s > 0.0) {
+    // time budget: run check_every iterations at a time and stop once the
+    // budget is spent; every instance stops by itself at maxiter, so the
+    // loop ends even without a deadline
+    const auto t0 = std::chrono::steady_clock::now();
+    while (act > 0) {
+      const int st = strom_solver_step(s, s->opt.check_every, stream, &act);
+      if (st != STROM_OK) return st;
+      const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (act > 0 && el >= s->opt.time_budget_s) {
+        out_of_time = true;
+        break;
+      }
+    }
+  } else {
+    const int st = strom_solver_step(s, s ? s->opt.maxiter : 0, stream, &act);
+    if (st != STROM_OK) return st;
+  }
   std::vector<uint8_t> flag(s->ninst);
   try {
     copy_d2h(flag.data(), s->inst_flag.p, s->ninst, s->stream);
@@ -768,6 +786,10 @@ extern "C" int strom_solve(strom_solver* s, void* stream) {
   }
   for (uint8_t f : flag)
     if (f == 2) { set_error("strom_solve: NaN or Inf in an instance"); return STROM_ERR_NUMERICAL; }
+  if (out_of_time) {
+    set_error("strom_solve: time budget exhausted (state and results valid up to the last iteration run)");
+    return STROM_ERR_TIMEOUT;
+  }
   for (uint8_t f : flag)
     if (f != 1) return STROM_MAXITER;
   return STROM_OK;
