@@ -58,6 +58,43 @@ def test_builder_matches_oracle(S, which):
     assert np.array_equal(a.row_clique, o.row_clique)
 
 
+def _autonomous():
+    """No control (du = 0): x_k = 0.9 x_{k-1}, one degree-1 inequality per clique."""
+    from workloads.poly import Poly
+    from workloads.problems import Clique, Problem
+    X0, X1 = Poly.var(2, 0), Poly.var(2, 1)
+    cl = [Clique(X0 * X0, [1.0 - X1], [X1 - 0.9 * X0] + ([X0 - 0.5] if k == 0 else [])) for k in range(3)]
+    return Problem("autonomous", 3, 1, 0, cl, R=1.0)
+
+
+def _no_inequalities():
+    p = wl.toy_problem(N=3)
+    for c in p.cliques:
+        c.g = []
+    return p
+
+
+@pytest.mark.parametrize("make", [lambda: wl.toy_problem(N=1), lambda: wl.pendulum_problem(N=1),
+                                  _no_inequalities, _autonomous],
+                         ids=["toy-N1", "pendulum-N1", "no-inequalities", "no-control"])
+def test_builder_matches_oracle_edge_cases(S, make):
+    """Degenerate shapes: one clique (no consensus rows), no localizing blocks, du = 0."""
+    p = make()
+    a = S.Problem(p).relax().export()
+    o = OR.relax(p)
+    assert np.array_equal(a.block_n, [b.n for b in o.blocks])
+    assert np.array_equal(a.rowptr, o.A.indptr) and np.array_equal(a.col, o.A.indices)
+    assert np.max(np.abs(a.val - o.A.data)) <= 1e-15 * np.max(np.abs(o.A.data))
+    assert np.max(np.abs(a.C - o.C)) <= 1e-15 * max(1.0, np.max(np.abs(o.C)))
+    assert np.array_equal(a.b, o.b)
+    assert np.array_equal(a.row_kind, o.row_kind) and np.array_equal(a.row_clique, o.row_clique)
+    kinds = np.bincount(o.row_kind, minlength=5)
+    if p.N == 1:
+        assert kinds[OR.KIND_CONS] == 0
+    if all(not c.g for c in p.cliques):
+        assert kinds[OR.KIND_INEQ] == 0 and all(b.kind == "M" for b in o.blocks)
+
+
 def test_problem_validation(S):
     p = wl.toy_problem(N=2)
     p.kappa = 3
