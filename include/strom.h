@@ -397,6 +397,29 @@ int strom_kernel_At(const strom_solver* s, const double* y_dev, double* x_dev, v
 int strom_kernel_solve(const strom_solver* s, const double* r_dev, double* y_dev, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Autotuning of the y-solve launch shape. Sec. 4 picks the implementation of
+ * the linear-system solve by measuring the alternatives (its hybrid
+ * CPU/GPU solve against GPU triangular solves); this call makes that choice
+ * per batch, on the device. When the instances share the factor of cliques
+ * 2..N (opt.share_tail), the chain solve can serve a tile of 1, 2, 4 or 8
+ * instances per CTA; all tiles give bit-identical y, so only the time
+ * differs. Each candidate tile (up to the batch size) runs the whole y-solve
+ * `reps` times on a scratch right-hand side, timed with CUDA events on the
+ * solver's stream; the fastest is kept for every later iteration (the
+ * captured iteration graph is rebuilt on the next step). Without a shared
+ * tail only the one-instance-per-CTA solve exists and nothing changes.
+ * The solver's state (X, S, y, sigma) is not touched. reps in 1..1000.
+ * Allocates two scratch vectors of m_total doubles for the duration of the
+ * call. Waits for `stream` (may be NULL) before timing. */
+typedef struct {
+  int32_t ncand;             /* candidates timed */
+  int32_t tile[4];           /* instances per CTA of each candidate */
+  double ms[4];              /* mean time of one y-solve (milliseconds) */
+  int32_t chosen;            /* tile kept */
+} strom_tune_report;
+int strom_solver_tune(strom_solver* s, int32_t reps, void* stream, strom_tune_report* out);
+
+/* ------------------------------------------------------------------------
  * PSD projection of a list of symmetric blocks given in svec form
  * (Sec. 4, parallel PSD cone projection): P = Q max(0, W) Q^T per block.
  * A plan uploads the block table once; execute may be called many times.

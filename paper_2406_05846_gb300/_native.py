@@ -74,6 +74,10 @@ PI8 = C.POINTER(C.c_int8)
 PU8 = C.POINTER(C.c_uint8)
 
 # name: (restype, argtypes)
+class strom_tune_report(C.Structure):
+    _fields_ = [("ncand", C.c_int32), ("tile", C.c_int32 * 4), ("ms", C.c_double * 4), ("chosen", C.c_int32)]
+
+
 SIGNATURES = {
     "strom_last_error": (C.c_char_p, []),
     "strom_version": (C.c_char_p, []),
@@ -108,6 +112,7 @@ SIGNATURES = {
     "strom_kernel_A": (C.c_int, [P, P, P, P]),
     "strom_kernel_At": (C.c_int, [P, P, P, P]),
     "strom_kernel_solve": (C.c_int, [P, P, P, P]),
+    "strom_solver_tune": (C.c_int, [P, C.c_int32, P, C.POINTER(strom_tune_report)]),
     "strom_batch_create": (C.c_int, [P, C.c_int32, C.POINTER(strom_options), C.POINTER(P)]),
     "strom_batch_destroy": (None, [P]),
     "strom_batch_submit": (C.c_int, [P, P, P, PD, PD, C.POINTER(C.c_uint64)]),

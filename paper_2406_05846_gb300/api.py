@@ -305,6 +305,13 @@ class Solver:
     def kernel_solve(self, r_ptr, y_ptr, stream=None):
         check(lib().strom_kernel_solve(self.handle, r_ptr, y_ptr, stream), "strom_kernel_solve")
 
+    def tune(self, reps=5, stream=None):
+        """strom_solver_tune: time the y-solve launch shapes and keep the fastest.
+        Returns ({tile: ms per y-solve}, chosen tile)."""
+        rep = N.strom_tune_report()
+        check(lib().strom_solver_tune(self.handle, int(reps), stream, C.byref(rep)), "strom_solver_tune")
+        return {rep.tile[i]: rep.ms[i] for i in range(rep.ncand)}, rep.chosen
+
 
 def _check_len(a, n, name):
     if a is not None and np.asarray(a).size != n:

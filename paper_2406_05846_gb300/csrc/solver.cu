@@ -914,6 +914,70 @@ extern "C" int strom_kernel_solve(const strom_solver* s, const double* r_dev, do
   });
 }
 
+namespace {
+struct EventPair {  // both events are destroyed even when creating the second one fails
+  cudaEvent_t a = nullptr, b = nullptr;
+  void create() {
+    STROM_CUDA(cudaEventCreate(&a));
+    STROM_CUDA(cudaEventCreate(&b));
+  }
+  ~EventPair() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
+}  // namespace
+
+extern "C" int strom_solver_tune(strom_solver* s, int32_t reps, void* stream, strom_tune_report* out) {
+  return guard([&] {
+    if (!s || !out || reps < 1 || reps > 1000) throw StatusError(STROM_ERR_INVALID, "strom_solver_tune: bad arguments");
+    std::memset(out, 0, sizeof(*out));
+    if (stream) STROM_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    cudaStream_t st = s->stream;
+    // candidate tiles: the multi-right-hand-side kernel needs the shared tail
+    std::vector<int> cand = {1};
+    if (s->shared_tail)
+      for (int r : {2, 4, 8})
+        if (r <= s->ninst) cand.push_back(r);
+    DevBuf<double> rhs, sol;
+    rhs.alloc(s->m);
+    sol.alloc(s->m);
+    std::vector<double> ones(s->m, 1.0);
+    copy_h2d(rhs.p, ones.data(), sizeof(double) * s->m, st);
+    YsolveDev yd = s->yd;
+    yd.inst_active = nullptr;
+    EventPair ev;
+    ev.create();
+    int best = s->yd.tile_r;
+    double best_ms = -1.0;
+    for (size_t c = 0; c < cand.size(); ++c) {
+      yd.tile_r = cand[c];
+      ysolve_apply(yd, s->ninst, s->max_group, rhs.p, sol.p, s->rho.p, st);  // warm-up
+      STROM_CUDA(cudaEventRecord(ev.a, st));
+      for (int k = 0; k < reps; ++k) ysolve_apply(yd, s->ninst, s->max_group, rhs.p, sol.p, s->rho.p, st);
+      STROM_CUDA(cudaEventRecord(ev.b, st));
+      STROM_CUDA(cudaEventSynchronize(ev.b));
+      float ms = 0.0f;
+      STROM_CUDA(cudaEventElapsedTime(&ms, ev.a, ev.b));
+      out->tile[c] = cand[c];
+      out->ms[c] = (double)ms / reps;
+      if (best_ms < 0.0 || out->ms[c] < best_ms) {
+        best_ms = out->ms[c];
+        best = cand[c];
+      }
+    }
+    out->ncand = (int32_t)cand.size();
+    out->chosen = best;
+    if (best != s->yd.tile_r) {
+      s->yd.tile_r = best;
+      // the captured iteration holds the old launch shape: capture again on the next step
+      if (s->graph) { STROM_CUDA(cudaGraphExecDestroy(s->graph)); s->graph = nullptr; }
+      if (s->graph_def) { STROM_CUDA(cudaGraphDestroy(s->graph_def)); s->graph_def = nullptr; }
+    }
+    return STROM_OK;
+  });
+}
+
 // helpers for the certificate (certify.cpp)
 namespace strom {
 struct CertDevice {

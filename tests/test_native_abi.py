@@ -95,6 +95,19 @@ def test_builder_matches_oracle_edge_cases(S, make):
         assert kinds[OR.KIND_INEQ] == 0 and all(b.kind == "M" for b in o.blocks)
 
 
+def test_tune_validates_arguments_without_a_gpu(S):
+    """strom_solver_tune rejects a null solver, a null report and reps outside
+    1..1000 before any CUDA call."""
+    import ctypes as C
+    from paper_2406_05846_gb300 import _native as N
+    L = S.lib()
+    rep = N.strom_tune_report()
+    assert L.strom_solver_tune(None, 5, None, C.byref(rep)) == -1
+    assert b"strom_solver_tune" in L.strom_last_error()
+    assert L.strom_solver_tune(None, 5, None, None) == -1
+    assert L.strom_solver_tune(None, 0, None, C.byref(rep)) == -1
+
+
 def test_problem_validation(S):
     p = wl.toy_problem(N=2)
     p.kappa = 3
