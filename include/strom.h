@@ -266,8 +266,9 @@ int strom_certify(strom_solver* s, int32_t i, const strom_problem* p, double ran
 int strom_certify_batch(strom_solver* s, const strom_problem* const* problems, double rank_tol, double xi_tol,
                         strom_certificate* out);
 
-/* Number of CUDA kernels libstrom has launched in this process (a graph
- * launch counts each of its kernel nodes). */
+/* Bookkeeping (no counterpart in the paper): number of CUDA kernels libstrom
+ * has launched in this process (a graph launch counts each of its kernel
+ * nodes). */
 uint64_t strom_launch_count(void);
 /* Bytes libstrom has copied host->device and device->host in this process. */
 void strom_transfer_bytes(uint64_t* h2d, uint64_t* d2h);
@@ -308,6 +309,10 @@ int strom_moment_rank_test(const double* M, int32_t nv, const uint8_t* vars, dou
  * or maxiter: their result and, when a problem was given, their certificate
  * are stored and the slot is reused at once. No slot waits for another, and
  * a request's arithmetic does not depend on what shares the batch with it.
+ * Each slot runs Algorithm 1 with the certificate of Sec. 2.2 / eq.
+ * (suboptimality-gap); the serving loop itself has no counterpart in the
+ * paper, whose nearest use is the MPC loop of Sec. 5 (one warm-started solve
+ * per control step).
  * ---------------------------------------------------------------------- */
 typedef struct strom_batch strom_batch;
 
