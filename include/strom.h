@@ -260,6 +260,24 @@ typedef struct {
 int strom_certify(strom_solver* s, int32_t i, const strom_problem* p, double rank_tol, double xi_tol,
                   strom_certificate* out, double* zbar, double* zhat);
 
+/* The host half of the certificate, from eigen data computed elsewhere (no
+ * GPU involved): the same extraction, rollout, lower bound and verdict as
+ * strom_certify, given for one instance of problem p its nblocks blocks in
+ * the builder's order (M_1, L_{1,*}, M_2, ...: block_n, block_kind 0 = moment
+ * / 1 = localizing, block_clique 0-based), and, packed block after block at
+ * offsets sum of previous block_n:
+ *   lamX  eigenvalues of each block of X, ascending;
+ *   topX  the eigenvector of each block's largest eigenvalue (any sign);
+ *   lamZ  eigenvalues of each block of Z = C - A^T y, ascending;
+ *   by    <b, y>.
+ * Errors: INVALID when the block list does not match the problem (one
+ * moment block of size (nv + 1)(nv + 2) / 2 per clique, as many localizing
+ * blocks per clique as it has inequalities). */
+int strom_certify_host(const strom_problem* p, int32_t nblocks, const int32_t* block_n, const int8_t* block_kind,
+                       const int32_t* block_clique, const double* lamX, const double* topX, const double* lamZ,
+                       double by, double rank_tol, double xi_tol, strom_certificate* out, double* zbar,
+                       double* zhat);
+
 /* The certificate of every instance of the solver; problems[i] describes
  * instance i. out: [count]. Eigenvalues of all blocks are computed in two
  * batched GPU launches; the rollout and bound run on the host. */

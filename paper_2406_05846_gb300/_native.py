@@ -106,6 +106,8 @@ SIGNATURES = {
     "strom_get_moment": (C.c_int, [P, C.c_int32, C.c_int32, PD]),
     "strom_get_kept_rows": (C.c_int, [P, C.c_int32, PU8]),
     "strom_certify": (C.c_int, [P, C.c_int32, P, C.c_double, C.c_double, C.POINTER(strom_certificate), PD, PD]),
+    "strom_certify_host": (C.c_int, [P, C.c_int32, PI32, C.POINTER(C.c_int8), PI32, PD, PD, PD, C.c_double,
+                                     C.c_double, C.c_double, C.POINTER(strom_certificate), PD, PD]),
     "strom_solver_nsvec_total": (C.c_int64, [P]),
     "strom_solver_m_total": (C.c_int64, [P]),
     "strom_solver_offsets": (C.c_int, [P, C.c_int32, PI64, PI64]),

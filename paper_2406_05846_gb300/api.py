@@ -195,6 +195,29 @@ class Certificate:
     zhat: np.ndarray
 
 
+def certify_host(problem: "Problem", block_n, block_kind, block_clique, lamX, topX, lamZ, by,
+                 rank_tol=1e-4, xi_tol=1e-2) -> Certificate:
+    """strom_certify_host: the host half of the certificate from eigen data
+    computed elsewhere (eigenvalues of X's and Z's blocks, top eigenvectors of
+    X's blocks, packed block after block; <b, y>)."""
+    bn = np.ascontiguousarray(block_n, np.int32)
+    bk = np.ascontiguousarray(block_kind, np.int8)
+    bc = np.ascontiguousarray(block_clique, np.int32)
+    tot = int(bn.sum())
+    lx, tx, lz = (np.ascontiguousarray(v, np.float64).ravel() for v in (lamX, topX, lamZ))
+    if not (len(bk) == len(bc) == len(bn)) or not (lx.size == tx.size == lz.size == tot):
+        raise ValueError("block lists must have one length and eigen data sum(block_n) entries")
+    nz = problem.N * (problem.dx + problem.du) + problem.dx
+    zb, zh = np.empty(nz), np.empty(nz)
+    c = N.strom_certificate()
+    check(lib().strom_certify_host(problem.handle, len(bn), _ptr(bn, C.c_int32), _ptr(bk, C.c_int8),
+                                   _ptr(bc, C.c_int32), _ptr(lx, C.c_double), _ptr(tx, C.c_double),
+                                   _ptr(lz, C.c_double), float(by), rank_tol, xi_tol, C.byref(c),
+                                   _ptr(zb, C.c_double), _ptr(zh, C.c_double)), "strom_certify_host")
+    return Certificate(c.max_ratio, c.lower_bound, c.phat, c.xi, c.hmax, c.gmin, bool(c.feasible),
+                       bool(c.rank_one), bool(c.certified), zb, zh)
+
+
 class Solver:
     """strom_solver: sGS-ADMM (Algorithm 1) on a batch of SDPs on the current GPU."""
 

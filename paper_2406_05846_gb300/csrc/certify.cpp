@@ -11,6 +11,8 @@
 //    gmax = sum_t |c_t| max(1,R)^deg(t) (an upper bound of max g on the box).
 #include <algorithm>
 #include <cmath>
+#include <stdexcept>
+#include <string>
 #include <vector>
 
 #include "internal.h"
@@ -233,6 +235,46 @@ extern "C" int strom_certify(strom_solver* s, int32_t i, const strom_problem* pr
   } catch (const std::exception& e) {
     set_error(std::string("strom_certify: ") + e.what());
     return STROM_ERR_CUDA;
+  }
+}
+
+extern "C" int strom_certify_host(const strom_problem* prob, int32_t nblocks, const int32_t* block_n,
+                                  const int8_t* block_kind, const int32_t* block_clique, const double* lamX,
+                                  const double* topX, const double* lamZ, double by, double rank_tol, double xi_tol,
+                                  strom_certificate* out, double* zbar_out, double* zhat_out) {
+  try {
+    if (!prob || !out || nblocks < 1 || !block_n || !block_kind || !block_clique || !lamX || !topX || !lamZ)
+      throw std::invalid_argument("bad arguments");
+    const Problem& p = prob->p;
+    const int nv = p.nv();
+    const int nmom = (nv + 1) * (nv + 2) / 2;
+    std::vector<int> n_mom(p.N, 0), n_loc(p.N, 0);
+    std::vector<int64_t> lo(nblocks);
+    int64_t acc = 0;
+    for (int b = 0; b < nblocks; ++b) {
+      const int k = block_clique[b];
+      if (k < 0 || k >= p.N || block_n[b] < 1) throw std::invalid_argument("block clique or size out of range");
+      if (block_kind[b] == 0) {
+        if (block_n[b] != nmom) throw std::invalid_argument("moment block of the wrong size");
+        ++n_mom[k];
+      } else if (block_kind[b] == 1) {
+        ++n_loc[k];
+      } else {
+        throw std::invalid_argument("block kind must be 0 (moment) or 1 (localizing)");
+      }
+      lo[b] = acc;
+      acc += block_n[b];
+    }
+    for (int k = 0; k < p.N; ++k)
+      if (n_mom[k] != 1 || n_loc[k] != (int)p.cl[k].g.size())
+        throw std::invalid_argument("blocks do not match the problem's cliques");
+    std::vector<int32_t> bn(block_n, block_n + nblocks), bc(block_clique, block_clique + nblocks);
+    std::vector<int8_t> bk(block_kind, block_kind + nblocks);
+    certify_one(p, bn, bk, bc, lo.data(), lamX, topX, lamZ, by, rank_tol, xi_tol, out, zbar_out, zhat_out);
+    return STROM_OK;
+  } catch (const std::exception& e) {
+    set_error(std::string("strom_certify_host: ") + e.what());
+    return STROM_ERR_INVALID;
   }
 }
 
