@@ -7,6 +7,7 @@ every moment matrix has rank one) on horizons 2 and 3.
 import numpy as np
 import pytest
 import scipy.optimize as so
+import scipy.sparse as sp
 
 import workloads as wl
 from oracle import certify as CE
@@ -118,3 +119,61 @@ def test_admm_detects_wrong_sign():
     bad_sdp.C = -bad_sdp.C
     bad = O.solve(O.ReducedSDP(bad_sdp, red.keep, red.A, red.b, red.blocks), O.Options(tol=1e-8, maxiter=20000))
     assert abs(bad.pobj - good.pobj) > 1e-2
+
+
+# --------------------------------------------------------------------------
+# closed forms of Algorithm 1 and of the residuals (eq. kkt-residual)
+# --------------------------------------------------------------------------
+def _trace_sdp(Cmats, seed=0):
+    """min <C, X> s.t. tr(X_beta) = 1 for every block, X_beta PSD: the optimum
+    of each block is lambda_min(C_beta), attained at v v^T (v its eigenvector),
+    and the dual is y_beta = lambda_min(C_beta), S_beta = C_beta - y_beta I."""
+    blocks, off, C, rows = [], 0, [], []
+    for k, Cm in enumerate(Cmats):
+        n = Cm.shape[0]
+        blocks.append(R.Block("M", k, -1, n, off))
+        C.append(R.svec(Cm))
+        rows.append((off, R.svec(np.eye(n))))
+        off += n * (n + 1) // 2
+    A = np.zeros((len(Cmats), off))
+    for i, (o, v) in enumerate(rows):
+        A[i, o:o + len(v)] = v
+    A = sp.csr_matrix(A)
+    sdp = R.SDP(blocks, off, np.concatenate(C), A, np.ones(len(Cmats)), np.zeros(len(Cmats), np.int8),
+                np.arange(len(Cmats)), len(Cmats), 0, 2, None)
+    return O.ReducedSDP(sdp, np.ones(len(Cmats), bool), A, sdp.b, sdp.block_slices())
+
+
+def test_algorithm1_reaches_the_closed_form_optimum():
+    rng = np.random.default_rng(21)
+    mats = []
+    for n in (3, 5, 8):
+        G = rng.standard_normal((n, n))
+        mats.append(0.5 * (G + G.T))
+    red = _trace_sdp(mats)
+    res = O.solve(red, O.Options(tol=1e-10, maxiter=20000))
+    assert res.converged
+    want = sum(np.linalg.eigvalsh(M)[0] for M in mats)
+    assert abs(res.pobj - want) <= 1e-8 * (1 + abs(want))
+    assert abs(res.dobj - want) <= 1e-8 * (1 + abs(want))
+    for k, M in enumerate(mats):
+        assert abs(res.y[k] - np.linalg.eigvalsh(M)[0]) <= 1e-7
+        b = red.blocks[k]
+        X = R.smat(res.X[b[0]:b[0] + b[1] * (b[1] + 1) // 2], b[1])
+        v = np.linalg.eigh(M)[1][:, 0]
+        assert np.max(np.abs(X - np.outer(v, v))) <= 1e-6
+
+
+def test_residuals_closed_form():
+    red = _trace_sdp([np.diag([1.0, -2.0]), np.diag([3.0, 4.0, 5.0])])
+    C = red.sdp.C
+    zx, zy = np.zeros(red.sdp.nsvec), np.zeros(red.m)
+    ep, ed, eg, pobj, dobj = O.residuals(red, C, zx, zy, zx)
+    nb, nc = np.linalg.norm(red.b), np.linalg.norm(C)
+    assert abs(ep - nb / (1 + nb)) < 1e-15 and abs(ed - nc / (1 + nc)) < 1e-15 and eg == 0.0
+    # at the exact primal-dual pair all three vanish
+    X = np.concatenate([R.svec(np.diag([0.0, 1.0])), R.svec(np.diag([1.0, 0.0, 0.0]))])
+    y = np.array([-2.0, 3.0])
+    S = C - red.A.T @ y
+    ep, ed, eg, pobj, dobj = O.residuals(red, C, X, y, S)
+    assert max(ep, ed, eg) < 1e-15 and pobj == dobj == 1.0
