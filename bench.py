@@ -103,9 +103,15 @@ class Clocks:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        return self.summarise(self.lines)
+
+    @staticmethod
+    def summarise(lines):
+        """Median and maximum SM clock and the throttle reasons seen active in
+        nvidia-smi CSV lines (the fields of Q, no header, no units)."""
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
