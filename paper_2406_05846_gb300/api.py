@@ -478,8 +478,9 @@ class PsdPlan:
     """strom_psd_plan: PSD projection of a fixed list of svec blocks."""
 
     def __init__(self, blk_off, blk_n, precision=N.STROM_PREC_FP64):
-        self._off = np.ascontiguousarray(blk_off, np.int64)
-        self._n = np.ascontiguousarray(blk_n, np.int32)
+        self._off = np.ascontiguousarray(blk_off, np.int64).ravel()
+        self._n = np.ascontiguousarray(blk_n, np.int32).ravel()
+        _check_blocks(self._off, self._n)
         h = C.c_void_p()
         check(lib().strom_psd_plan_create(_ptr(self._off, C.c_int64), _ptr(self._n, C.c_int32), len(self._n),
                                           precision, C.byref(h)), "strom_psd_plan_create")
@@ -523,8 +524,15 @@ def transfer_bytes():
     return int(h.value), int(d.value)
 
 
+def _check_blocks(off, n):
+    """One offset per block size, so the library never reads past either array."""
+    if off.size != n.size:
+        raise ValueError("blk_off has %d entries but blk_n has %d" % (off.size, n.size))
+
+
 def kernel_psd_project(xb_ptr, blk_off, blk_n, precision, out_ptr, stream=None):
-    off = np.ascontiguousarray(blk_off, np.int64)
-    n = np.ascontiguousarray(blk_n, np.int32)
+    off = np.ascontiguousarray(blk_off, np.int64).ravel()
+    n = np.ascontiguousarray(blk_n, np.int32).ravel()
+    _check_blocks(off, n)
     check(lib().strom_kernel_psd_project(xb_ptr, _ptr(off, C.c_int64), _ptr(n, C.c_int32), len(n), precision,
                                          out_ptr, stream), "strom_kernel_psd_project")

@@ -142,6 +142,15 @@ def test_binding_checks_array_lengths(S):
         api._check_len(np.zeros(4), 5, "X0")
 
 
+def test_binding_checks_block_tables(S):
+    """PSD plans and the one-shot projection refuse offset and size tables of
+    different lengths before the library would read past the shorter one."""
+    with pytest.raises(ValueError, match="blk_off"):
+        S.PsdPlan([0, 3], [2], 0)
+    with pytest.raises(ValueError, match="blk_off"):
+        S.kernel_psd_project(0, [0], [2, 2], 0, 0)
+
+
 def test_builder_reproduces_paper_pendulum_sizes(S):
     """Table 1's pendulum row and the sizes quoted in Sec. 1, from the C++ builder."""
     import test_oracle_relax as T
