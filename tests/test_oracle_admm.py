@@ -177,3 +177,37 @@ def test_residuals_closed_form():
     S = C - red.A.T @ y
     ep, ed, eg, pobj, dobj = O.residuals(red, C, X, y, S)
     assert max(ep, ed, eg) < 1e-15 and pobj == dobj == 1.0
+
+
+def test_paper_pendulum_relaxation_matches_brute_force():
+    """The paper's own pendulum model (variational integrator on SO(2)) at N = 2:
+    the relaxation is tight (rank 1) and its optimum equals a brute-force search
+    over both controls of the explicit simulation, with f_c >= f_c,min enforced."""
+    from test_oracle_relax import _paper_pend_rollout
+    p = wl.paper_pendulum_problem(N=2, theta0=0.3, thetadot0=0.7)
+    fc_min = p.meta["fc_min"]
+
+    def cost(U):
+        U = np.clip(U, -1, 1)
+        with np.errstate(invalid="ignore"):
+            z = _paper_pend_rollout(p, U)
+        fc = np.array([z[5 * k + 2] for k in range(1, p.N + 1)])    # x_k = (r_c, r_s, f_c, f_s) at z[5k:5k+4]
+        if not np.all(np.isfinite(z)) or np.any(fc < fc_min):
+            return np.inf
+        return p.objective(z)
+    g = np.linspace(-1, 1, 201)
+    best, u0 = np.inf, None
+    for a in g:
+        for b in g:
+            v = cost([a, b])
+            if v < best:
+                best, u0 = v, np.array([a, b])
+    r = so.minimize(cost, u0, bounds=[(-1, 1)] * 2, method="L-BFGS-B", options=dict(ftol=1e-15, gtol=1e-12))
+    pbf = min(r.fun, best)
+    red = O.reduce(R.relax(p))
+    res = O.solve(red, O.Options(tol=1e-9, maxiter=40000))
+    cert = CE.certify(p, red, res.X, res.y)
+    assert res.converged and cert.rank_one and cert.feasible
+    assert res.pobj <= pbf + 1e-6 * (1 + abs(pbf))
+    assert abs(res.pobj - pbf) <= 1e-6 * (1 + abs(pbf))
+    assert cert.lower_bound <= pbf + 1e-9
