@@ -344,7 +344,9 @@ int strom_batch_submit(strom_batch* b, const strom_sdp* sdp, const strom_problem
 int strom_batch_step(strom_batch* b, int32_t iters, void* stream, int32_t* n_running, int32_t* n_queued);
 /* STROM_OK once the request finished (outputs filled; c only if a problem
  * was given), STROM_PENDING before. latency_s: submit to retirement;
- * service_s: admission into a slot to retirement. Any output may be NULL. */
+ * service_s: admission into a slot to retirement. Any output may be NULL.
+ * A finished request's result (about 200 bytes) stays readable, and held,
+ * until the batch is destroyed. */
 int strom_batch_poll(strom_batch* b, uint64_t ticket, strom_result* r, strom_certificate* c, double* latency_s,
                      double* service_s);
 /* ------------------------------------------------------------------------
