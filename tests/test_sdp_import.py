@@ -6,6 +6,7 @@ import pytest
 
 import workloads as wl
 from oracle import relax as OR
+from oracle import sgs_admm as OA
 
 
 @pytest.fixture(scope="module")
@@ -137,3 +138,51 @@ def test_rejects_malformed_input(S):
     Cn = a.C.copy()
     Cn[3] = np.nan
     bad("non-finite", C_=Cn)
+
+
+def test_star_elimination_solves_A_At(S):
+    """The y-solve's algebra on CPU, from the library's exported star data: the
+    Gram A_o diag(omega) A_o^T of the other rows is the exact Schur complement of
+    the A_mom rows in A A^T (Sherman-Morrison per star), and the star
+    elimination -> Schur solve -> back substitution sequence (the steps of the
+    GPU y-solve) returns (A_K A_K^T)^{-1} r_K of the row-reduced system (eq.
+    solve-y1)."""
+    import scipy.sparse as sp
+    p = wl.pendulum_problem(N=3, theta0=0.1)
+    sd = S.Problem(p).relax()
+    a, st = sd.export(), sd.star_data()
+    A = sp.csr_matrix((a.val, a.col, a.rowptr), shape=(len(a.rowptr) - 1, sd.nsvec))
+    mom = a.row_kind == 0
+    As, Ao = A[mom], A[~mom]
+    Gss, Gso, Goo = (As @ As.T).toarray(), (As @ Ao.T).toarray(), (Ao @ Ao.T).toarray()
+    schur = Goo - Gso.T @ np.linalg.solve(Gss, Gso)
+    gram = (Ao @ sp.diags(st.omega) @ Ao.T).toarray()
+    assert np.max(np.abs(schur - gram)) <= 1e-14 * np.max(np.abs(schur))
+    # the whole solve on the kept rows, against the oracle's sparse LU
+    red = OA.reduce(OR.relax(p))
+    keep = red.keep
+    assert np.all(keep[mom])                              # A_mom rows are always independent
+    r = np.random.default_rng(5).standard_normal(A.shape[0])
+    r[~keep] = 0.0
+    rho = np.zeros(sd.nsvec)
+    for c in range(st.rep.size):                          # star elimination (forward)
+        q = st.row[st.ptr[c]:st.ptr[c + 1]]
+        acc = np.sum(r[q] * st.inv_s2[st.ptr[c]:st.ptr[c + 1]])
+        rho[st.rep[c]] = st.c[c] * acc / (1.0 + st.c[c] * st.dsum[c]) * st.inv_rep_s[st.rep[c]]
+    oth = np.nonzero(~mom)[0]
+    ko = keep[oth]
+    t = r[oth] + Ao @ rho                                 # right-hand side of the Schur system
+    y = np.zeros(A.shape[0])
+    y[oth[ko]] = np.linalg.solve(gram[np.ix_(ko, ko)], t[ko])
+    AoT = Ao.T.tocsr()
+    for c in range(st.rep.size):                          # back substitution of the stars
+        sl = slice(st.ptr[c], st.ptr[c + 1])
+        q, is2 = st.row[sl], st.inv_s2[sl]
+        rep = st.rep[c]
+        gam = (AoT[rep] @ y[oth])[0] * st.inv_rep_s[rep]
+        su = np.sum((r[q] + st.c[c] * gam) * is2)
+        corr = st.c[c] * su / (1.0 + st.c[c] * st.dsum[c])
+        y[q] = (r[q] + st.c[c] * gam) * is2 - is2 * corr
+    want = OA.YSolver(red.A)(r[keep])
+    assert np.linalg.norm(y[keep] - want) <= 1e-10 * np.linalg.norm(want)
+    assert np.all(y[~keep] == 0.0)
