@@ -108,6 +108,22 @@ def test_tune_validates_arguments_without_a_gpu(S):
     assert L.strom_solver_tune(None, 0, None, C.byref(rep)) == -1
 
 
+def test_default_options_follow_the_same_readings_as_the_oracle(S):
+    """Algorithm 1's inputs and the sigma rule are readings of the paper (it
+    fixes only tau in (0, 2) and sigma > 0); the library's defaults and the
+    oracle's must be the same readings, or whole-solve parity would compare
+    two different methods."""
+    from oracle import sgs_admm as OA
+    o, ref = S.default_options(), OA.Options()
+    for k in ("sigma0", "tau", "sigma_every", "sigma_ratio", "sigma_factor", "sigma_min", "sigma_max"):
+        assert getattr(o, k) == getattr(ref, k), k
+    assert o.rank_tol == OA.RANK_TOL
+    assert 0 < o.tau < 2 and o.sigma0 > 0
+    assert o.time_budget_s == 0.0 and S.default_options(time_budget_s=2.5).time_budget_s == 2.5
+    with pytest.raises(KeyError):
+        S.default_options(no_such_option=1)
+
+
 def test_problem_validation(S):
     p = wl.toy_problem(N=2)
     p.kappa = 3
