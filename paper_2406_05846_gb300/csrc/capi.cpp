@@ -53,7 +53,10 @@ extern "C" int strom_problem_create(const strom_problem_desc* d, strom_problem**
     if (d->kappa != 2) throw std::invalid_argument("relaxation order kappa must be 2");
     if (!(d->R > 0)) throw std::invalid_argument("bound R must be positive");
     const int nv = 2 * d->dx + d->du;
-    if (nv > 16) throw std::invalid_argument("at most 16 variables per clique");
+    // the builder takes cliques of up to 21 variables (moment blocks up to
+    // s(21, 2) = 253); the solver's PSD kernels take blocks up to 160, i.e.
+    // cliques of up to 16 variables, and strom_solver_create checks that
+    if (nv > 21) throw std::invalid_argument("at most 21 variables per clique");
     std::unique_ptr<strom_problem> p(new strom_problem());
     p->p.N = d->N; p->p.dx = d->dx; p->p.du = d->du; p->p.kappa = d->kappa; p->p.R = d->R;
     for (int k = 0; k < d->N; ++k) {

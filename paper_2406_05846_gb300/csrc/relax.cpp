@@ -64,13 +64,21 @@ inline int64_t svec_index(int i, int j) {
 }
 inline double svec_scale(int i, int j) { return i == j ? 1.0 : 1.0 / std::sqrt(2.0); }
 
-using Key = uint64_t;  // 4 bits per variable, nv <= 16
+// A monomial packed into 64 bits: 4 bits per variable up to 16 variables,
+// 3 bits per variable for 17..21. Every monomial the relaxation forms has
+// total degree <= 2 kappa = 4 (the degrees of f, g and h are checked on
+// input), so no exponent exceeds 4 and a sum of two keys never carries into
+// the next variable's field.
+using Key = uint64_t;
+constexpr int kMaxCliqueVars = 21;
+inline int key_bits(int nv) { return nv <= 16 ? 4 : 3; }
 inline Key key_of(const uint8_t* e, int nv) {
+  const int b = key_bits(nv);
   Key k = 0;
-  for (int i = 0; i < nv; ++i) k |= (Key)e[i] << (4 * i);
+  for (int i = 0; i < nv; ++i) k |= (Key)e[i] << (b * i);
   return k;
 }
-inline Key key_add(Key a, Key b) { return a + b; }  // exponents stay < 16
+inline Key key_add(Key a, Key b) { return a + b; }
 
 struct MomentIndex {
   int nv, n;
@@ -107,7 +115,7 @@ std::vector<Term> terms_of(const Poly& p, int nv) {
 Sdp* build_relaxation(const Problem& p) {
   const int N = p.N, nv = p.nv(), kappa = p.kappa, dx = p.dx;
   if (kappa != 2) throw std::runtime_error("relaxation order kappa must be 2");
-  if (nv > 16) throw std::runtime_error("at most 16 variables per clique");
+  if (nv > kMaxCliqueVars) throw std::runtime_error("at most 21 variables per clique");
   MomentIndex mi(nv, kappa);
   const int nM = mi.n;
   Sdp* s = new Sdp();

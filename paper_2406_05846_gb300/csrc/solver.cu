@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <memory>
+#include <string>
 #include <vector>
 
 #include "admm.cuh"
@@ -456,6 +457,13 @@ extern "C" int strom_solver_create(const strom_sdp* const* sdps, int32_t count, 
     if (!(o.tol > 0) || o.maxiter < 1 || !(o.sigma0 > 0) || !(o.tau > 0 && o.tau < 2) || !(o.rank_tol > 0) ||
         o.precision < 0 || o.precision > 2 || o.check_every < 1 || o.eig_warm_period < 0)
       throw StatusError(STROM_ERR_INVALID, "strom_solver_create: invalid options");
+    // the PSD kernels keep a block of up to 160 rows in shared memory
+    for (int i = 0; i < count; ++i)
+      for (int32_t n : sdps[i]->s->block_n)
+        if (n < 1 || n > 160)
+          throw StatusError(STROM_ERR_INVALID, "strom_solver_create: a block of size " + std::to_string(n) +
+                                                   "; the solver takes blocks of 1..160 (cliques of at most 16 "
+                                                   "variables)");
     STROM_CUDA(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
     solver_setup(s.get(), sdps, count);
     *out = s.release();

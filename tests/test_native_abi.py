@@ -124,6 +124,33 @@ def test_default_options_follow_the_same_readings_as_the_oracle(S):
         S.default_options(no_such_option=1)
 
 
+@pytest.mark.parametrize("model", ["landing", "flying"])
+def test_builder_on_the_paper_robots(S, model):
+    """18- and 20-variable cliques (monomial keys of 3 bits per variable):
+    bit-exact parity with the oracle at N = 3, Table 1's sizes at the paper's
+    horizon, and a solver that refuses their 190 / 231 blocks (the PSD
+    kernels take up to 160) before touching the GPU."""
+    import test_oracle_relax as T
+    mk = getattr(wl, T.PAPER_ROBOTS[model])
+    small = mk(N=3)
+    a = S.Problem(small).relax().export()
+    o = OR.relax(small)
+    assert np.array_equal(a.block_n, [b.n for b in o.blocks])
+    assert np.array_equal(a.rowptr, o.A.indptr) and np.array_equal(a.col, o.A.indices)
+    assert np.max(np.abs(a.val - o.A.data)) <= 1e-15 * np.max(np.abs(o.A.data))
+    assert np.max(np.abs(a.C - o.C)) <= 1e-15 * max(1.0, np.max(np.abs(o.C)))
+    assert np.array_equal(a.b, o.b) and np.array_equal(a.row_kind, o.row_kind)
+    want = T.paper_robot_sizes()[model]
+    sd = S.Problem(mk()).relax()
+    e = sd.export()
+    assert sd.info.m == want["m"][0], want["m"][1]
+    assert int(np.sum(e.block_kind == 0)) == want["nM"][0] and int(np.sum(e.block_kind == 1)) == want["nL"][0]
+    assert set(e.block_n.tolist()) == {want["sizeM"][0], want["sizeL"][0]}
+    from paper_2406_05846_gb300._native import StromError
+    with pytest.raises(StromError, match="1..160"):
+        S.Solver([S.Problem(small).relax()])
+
+
 def test_problem_validation(S):
     p = wl.toy_problem(N=2)
     p.kappa = 3
@@ -133,6 +160,10 @@ def test_problem_validation(S):
     p.cliques[0].g.append(wl.Poly.var(3, 0) ** 3)   # cubic inequality: degree too high
     with pytest.raises(RuntimeError, match="degree"):
         S.Problem(p)
+    from workloads.problems import Clique, Problem   # 22 variables per clique: beyond the 64-bit monomial keys
+    x = wl.Poly.var(22, 0)
+    with pytest.raises(RuntimeError, match="21 variables"):
+        S.Problem(Problem("wide", 1, 10, 2, [Clique(x * x, [], [])]))
 
 
 def test_no_gpu_no_fallback(S):

@@ -272,3 +272,75 @@ def test_paper_pendulum_lifting_feasible():
         assert all(g.evaluate(zk) >= -1e-12 for g in c.g)
     z[5] += 1e-3                                      # break r_c of x_1
     assert np.max(np.abs(sdp.A @ R.lift_rank1(p, sdp, z) - sdp.b)) > 1e-5
+
+
+# --------------------------------------------------------------------------
+# the paper's vehicle landing and flying robot reproduce the printed sizes
+# --------------------------------------------------------------------------
+def paper_robot_sizes():
+    out = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "paper_robot_sizes.txt")):
+        if line.strip() and not line.startswith("#"):
+            model, k, v, cite = (x.strip() for x in line.split("|"))
+            out.setdefault(model, {})[k] = (int(v), cite)
+    return out
+
+
+PAPER_ROBOTS = {"landing": "paper_landing_problem", "flying": "paper_flying_robot_problem"}
+
+
+@pytest.mark.parametrize("model", ["landing", "flying"])
+def test_paper_robot_sizes(model):
+    """Under the equality reading of the paper's pendulum (circles of x_{k-1}
+    in cliques k >= 2, x_0 fixed by linear equalities) and with the printed
+    number of localizing matrices, the oracle's SDP has every size of the
+    model's Table 1 row, m included."""
+    want = paper_robot_sizes()[model]
+    p = getattr(wl, PAPER_ROBOTS[model])()
+    assert (p.dx, p.du) == (want["dx"][0], want["du"][0])
+    sdp = R.relax(p)
+    M = [b for b in sdp.blocks if b.kind == "M"]
+    L = [b for b in sdp.blocks if b.kind == "L"]
+    assert len(M) == want["nM"][0], want["nM"][1]
+    assert {b.n for b in M} == {want["sizeM"][0]}, want["sizeM"][1]
+    assert len(L) == want["nL"][0], want["nL"][1]
+    assert {b.n for b in L} == {want["sizeL"][0]}, want["sizeL"][1]
+    assert sdp.m == want["m"][0], want["m"][1]
+
+
+def flying_robot_rollout(p, U, dt=0.2, alpha=0.2, beta=0.2, r_max=10.0, v_max=10.0, u_max=8.0,
+                         x0=5.0, y0=-5.0, theta0=0.3):
+    """Explicit simulation of the flying robot in physical units (controls U in
+    [-1, 1]^4 map to u in [0, u_max]); returns the rescaled global vector."""
+    rx, ry, vx, vy = x0, y0, 0.0, 0.0
+    rc, rs, fc, fs = np.cos(theta0), np.sin(theta0), 1.0, 0.0
+    scale = np.array([r_max, r_max, v_max, v_max, 1, 1, 1, 1])
+    z = list(np.array([rx, ry, vx, vy, rc, rs, fc, fs]) / scale)
+    for Uk in U:
+        u = 0.5 * u_max * (np.asarray(Uk) + 1.0)
+        T = u[0] - u[1] + u[2] - u[3]
+        rx_n, ry_n = rx + dt * vx, ry + dt * vy
+        vx_n, vy_n = vx + dt * T * rc, vy + dt * T * rs
+        fs_n = fs + dt * dt * alpha * (u[1] - u[0]) + dt * dt * beta * (u[2] - u[3])
+        fc_n = np.sqrt(1.0 - fs_n * fs_n)
+        rc_n, rs_n = rc * fc - rs * fs, rs * fc + rc * fs
+        rx, ry, vx, vy, rc, rs, fc, fs = rx_n, ry_n, vx_n, vy_n, rc_n, rs_n, fc_n, fs_n
+        z += list(Uk) + list(np.array([rx, ry, vx, vy, rc, rs, fc, fs]) / scale)
+    return np.array(z)
+
+
+def test_paper_flying_robot_lifting_feasible():
+    """A rollout of the flying robot's dynamics, lifted to rank-1 moment
+    matrices, satisfies every row; its cost is <C, X>."""
+    rng = np.random.default_rng(6)
+    p = wl.paper_flying_robot_problem(N=4)
+    U = rng.uniform(-0.3, 0.3, size=(4, 4))
+    z = flying_robot_rollout(p, U)
+    sdp = R.relax(p)
+    X = R.lift_rank1(p, sdp, z)
+    assert np.max(np.abs(sdp.A @ X - sdp.b)) < 1e-12
+    assert abs(sdp.C @ X - p.objective(z)) < 1e-12 * (1 + abs(p.objective(z)))
+    for k, c in enumerate(p.cliques):
+        assert all(g.evaluate(p.clique_vars(z, k)) >= -1e-12 for g in c.g)
+    z[12 + 2] += 1e-4                  # v_x of x_1 (x_1 starts at z[12])
+    assert np.max(np.abs(sdp.A @ R.lift_rank1(p, sdp, z) - sdp.b)) > 1e-7

@@ -314,3 +314,153 @@ def problem_batch(kind: str, B: int, seed: int = BASE_SEED, **kw):
         else:
             raise ValueError(kind)
     return out
+
+
+# --------------------------------------------------------------------------
+# the paper's vehicle landing and flying robot (App. "Vehicle Landing",
+# "Flying Robot"): state x = (r_x, r_y, v_x, v_y, r_c, r_s, f_c, f_s),
+# attitude and its step rotation on SO(2) as in the paper's pendulum
+# --------------------------------------------------------------------------
+def _affine(v, lo, hi):
+    """Physical value of a variable rescaled to [-1, 1] from [lo, hi]."""
+    return 0.5 * (hi - lo) * v + 0.5 * (hi + lo)
+
+
+def _so2_robot(N, nu, dt, theta0, thetadot0, x0, y0, vx0, vy0, box, u_max, fc_min, goal, Pf, dyn, extra_g, name):
+    """Clique k: (x_{k-1}, u_{k-1}, x_k) with 2 * 8 + nu variables, rescaled to
+    [-1, 1] by `box` = ((lo, hi) of r_x, r_y, v_x, v_y) and u_i in [0, u_max].
+
+    Equalities of clique k: the translational dynamics `dyn` (physical
+    variables), the attitude update r_k = r_{k-1} * f_{k-1} on SO(2), the
+    circles of r and f for x_k and, for k >= 2, for x_{k-1}; x_0 is fixed by
+    eight linear equalities in clique 1 (the reading under which the
+    paper's pendulum reproduces its printed sizes). Inequalities of clique k:
+    u_i (u_max - u_i) >= 0 for u_{k-1}, the boxes of r_x, r_y, v_x, v_y and
+    f_c >= f_c,min for x_k; then `extra_g` more, as described by the caller.
+    Cost: the LQR-style loss to `goal` with identity weights after rescaling,
+    P_f on x_N.
+    """
+    dx = 8
+    nv = 2 * dx + nu
+    V = [Poly.var(nv, i) for i in range(nv)]
+    X0, U, X1 = V[:dx], V[dx:dx + nu], V[dx + nu:]
+
+    def phys(X):
+        return [_affine(X[i], *box[i]) for i in range(4)] + list(X[4:])
+
+    def scaled_state(vals):
+        return [(vals[i] - 0.5 * (box[i][1] + box[i][0])) / (0.5 * (box[i][1] - box[i][0])) for i in range(4)] \
+            + list(vals[4:])
+
+    P0, P1 = phys(X0), phys(X1)
+    u = [_affine(Ui, 0.0, u_max) for Ui in U]
+    g_target = scaled_state(goal)
+    init = scaled_state([x0, y0, vx0, vy0, np.cos(theta0), np.sin(theta0), np.cos(dt * thetadot0),
+                         np.sin(dt * thetadot0)])
+    rx0, ry0, vx_0, vy_0, rc0, rs0, fc0, fs0 = P0
+    rx1, ry1, vx_1, vy_1, rc1, rs1, fc1, fs1 = P1
+    raw = []
+    for k in range(1, N + 1):
+        f = sum((xi - t) * (xi - t) for xi, t in zip(X0, g_target)) + sum(Ui * Ui for Ui in U)
+        if k == N:
+            f = f + Pf * sum((xi - t) * (xi - t) for xi, t in zip(X1, g_target))
+        h = dyn(P0, P1, u) + [rc1 - (rc0 * fc0 - rs0 * fs0), rs1 - (rs0 * fc0 + rc0 * fs0),
+                               rc1 * rc1 + rs1 * rs1 - 1.0, fc1 * fc1 + fs1 * fs1 - 1.0]
+        if k >= 2:
+            h += [rc0 * rc0 + rs0 * rs0 - 1.0, fc0 * fc0 + fs0 * fs0 - 1.0]
+        else:
+            h += [X0[i] - init[i] for i in range(dx)]
+        gg = [ui * (u_max - ui) for ui in u]
+        gg += [1.0 - X1[i] * X1[i] for i in range(4)]
+        gg += [fc1 - fc_min]
+        gg += extra_g(k, X0)
+        raw.append((f, gg, h))
+    fscale = 1.0 / max(f.max_abs_coef() for f, _, _ in raw)
+    cl = [Clique(f * fscale, [p.normalized() for p in gg], [p.normalized() for p in h]) for f, gg, h in raw]
+    return Problem(name, N, dx, nu, cl, R=1.0, meta=dict(dt=dt, theta0=theta0, fscale=fscale))
+
+
+def _spread_previous_state_bounds(N, total):
+    """`total` bounds 1 - z^2 >= 0 on variables of x_{k-1} in cliques 2..N, as
+    evenly as possible (earlier cliques take the remainder), variables taken
+    in state order and cycling. They are implied by the box and circle
+    constraints of the clique before, so the trajectory problem is unchanged."""
+    counts = [0] * (N + 1)
+    for j in range(total):
+        counts[2 + j % (N - 1)] += 1
+
+    def extra(k, X0):
+        return [1.0 - X0[j % 8] * X0[j % 8] for j in range(counts[k])]
+    return extra
+
+
+def _extra_count(N, n_localizing, listed, N_paper, printed):
+    """Localizing constraints beyond the `listed` per clique: n_localizing -
+    listed N when given; by default the printed surplus at the paper's
+    horizon, scaled by (N - 1) / (N_paper - 1) at other horizons."""
+    if N < 2:
+        return 0
+    if n_localizing is not None:
+        return max(0, n_localizing - listed * N)
+    return int(round((printed - listed * N_paper) * (N - 1) / (N_paper - 1)))
+
+
+def paper_landing_problem(N: int = 50, dt: float = 0.2, theta0: float = 0.1, thetadot0: float = 0.0,
+                          x0: float = 20.0, y0: float = 100.0, vx0: float = 0.0, vy0: float = -5.0,
+                          m: float = 1.0, inertia: float = 50.0, lever: float = 5.0, g: float = 9.8,
+                          fc_min: float = 0.7, rx_max: float = 100.0, ry_min: float = 10.0, ry_max: float = 120.0,
+                          v_max: float = 20.0, u_max: float = 8.0, Pf: float = 10.0,
+                          n_localizing: int | None = None) -> Problem:
+    """The vehicle landing of the paper's appendix, 18-variable cliques (moment
+    blocks s(18, 2) = 190, localizing blocks s(18, 1) = 19).
+
+      m (v_x,k - v_x,k-1) = -dt (u_1 + u_2) r_s,k-1
+      m (v_y,k - v_y,k-1) = dt ((u_1 + u_2) r_c,k-1 - m g)      (the printed line
+                                                                 drops dt on m g)
+      I (f_s,k - f_s,k-1) = L dt^2 (u_2 - u_1);  r_k = r_k-1 + dt v_k-1
+    Goal: x = 0, y = 10, theta = 0 at rest. The appendix lists seven
+    inequalities per clique (350 for N = 50) and states 499 localizing
+    matrices; the other 149 are read as bounds on the previous state (see
+    _spread_previous_state_bounds; n_localizing sets the total). With N = 50
+    the SDP has Table 1's sizes.
+    """
+    box = ((-rx_max, rx_max), (ry_min, ry_max), (-v_max, v_max), (-v_max, v_max))
+
+    def dyn(P0, P1, u):
+        rx0, ry0, vx0_, vy0_, rc0, rs0, fc0, fs0 = P0
+        rx1, ry1, vx1, vy1, rc1, rs1, fc1, fs1 = P1
+        T = u[0] + u[1]
+        return [rx1 - rx0 - dt * vx0_, ry1 - ry0 - dt * vy0_, m * (vx1 - vx0_) + dt * T * rs0,
+                m * (vy1 - vy0_) - dt * (T * rc0 - m * g), inertia * (fs1 - fs0) - lever * dt * dt * (u[1] - u[0])]
+    extra = _spread_previous_state_bounds(N, _extra_count(N, n_localizing, listed=7, N_paper=50, printed=499))
+    return _so2_robot(N, 2, dt, theta0, thetadot0, x0, y0, vx0, vy0, box, u_max, fc_min,
+                      (0.0, 10.0, 0.0, 0.0, 1.0, 0.0, 1.0, 0.0), Pf, dyn, extra, "paper_landing")
+
+
+def paper_flying_robot_problem(N: int = 60, dt: float = 0.2, theta0: float = 0.3, thetadot0: float = 0.0,
+                               x0: float = 5.0, y0: float = -5.0, vx0: float = 0.0, vy0: float = 0.0,
+                               alpha: float = 0.2, beta: float = 0.2, fc_min: float = 0.7, r_max: float = 10.0,
+                               v_max: float = 10.0, u_max: float = 8.0, Pf: float = 10.0,
+                               n_localizing: int | None = None) -> Problem:
+    """The flying robot of the paper's appendix, 20-variable cliques (moment
+    blocks s(20, 2) = 231, localizing blocks s(20, 1) = 21).
+
+      v_k - v_k-1 = dt (u_1 - u_2 + u_3 - u_4) (r_c, r_s)_k-1
+      f_s,k - f_s,k-1 = dt^2 alpha (u_2 - u_1) + dt^2 beta (u_3 - u_4)   (as printed)
+      r_k = r_k-1 + dt v_k-1
+    Goal: the origin at rest with theta = 0. The appendix lists nine
+    inequalities per clique (540 for N = 60) and states 659 localizing
+    matrices; the other 119 are read as bounds on the previous state. With
+    N = 60 the SDP has Table 1's sizes.
+    """
+    box = ((-r_max, r_max), (-r_max, r_max), (-v_max, v_max), (-v_max, v_max))
+
+    def dyn(P0, P1, u):
+        rx0, ry0, vx0_, vy0_, rc0, rs0, fc0, fs0 = P0
+        rx1, ry1, vx1, vy1, rc1, rs1, fc1, fs1 = P1
+        T = u[0] - u[1] + u[2] - u[3]
+        return [rx1 - rx0 - dt * vx0_, ry1 - ry0 - dt * vy0_, vx1 - vx0_ - dt * T * rc0, vy1 - vy0_ - dt * T * rs0,
+                fs1 - fs0 - dt * dt * alpha * (u[1] - u[0]) - dt * dt * beta * (u[2] - u[3])]
+    extra = _spread_previous_state_bounds(N, _extra_count(N, n_localizing, listed=9, N_paper=60, printed=659))
+    return _so2_robot(N, 4, dt, theta0, thetadot0, x0, y0, vx0, vy0, box, u_max, fc_min,
+                      (0.0, 0.0, 0.0, 0.0, 1.0, 0.0, 1.0, 0.0), Pf, dyn, extra, "paper_flying_robot")
