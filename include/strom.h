@@ -77,7 +77,10 @@ typedef struct {
 typedef struct strom_problem strom_problem;
 
 /* Copies the description. Errors: INVALID (kappa != 2, a degree out of range,
- * an exponent tuple of the wrong length, N < 1). */
+ * an exponent tuple of the wrong length, N < 1, more than 21 variables per
+ * clique). The relaxation builder takes cliques of up to 21 variables; the
+ * solver takes blocks of up to 160 rows, i.e. cliques of up to 16 variables
+ * (strom_solver_create refuses larger blocks). */
 int strom_problem_create(const strom_problem_desc* desc, strom_problem** out);
 void strom_problem_destroy(strom_problem* p);
 
