@@ -344,3 +344,43 @@ def test_paper_flying_robot_lifting_feasible():
         assert all(g.evaluate(p.clique_vars(z, k)) >= -1e-12 for g in c.g)
     z[12 + 2] += 1e-4                  # v_x of x_1 (x_1 starts at z[12])
     assert np.max(np.abs(sdp.A @ R.lift_rank1(p, sdp, z) - sdp.b)) > 1e-7
+
+
+def landing_rollout(U, dt=0.2, m=1.0, inertia=50.0, lever=5.0, g=9.8, rx_max=100.0, ry_min=10.0, ry_max=120.0,
+                    v_max=20.0, u_max=8.0, x0=20.0, y0=100.0, vx0=0.0, vy0=-5.0, theta0=0.1):
+    """Explicit simulation of the vehicle landing in physical units (U in
+    [-1, 1]^2 maps to u in [0, u_max]); returns the rescaled global vector."""
+    rx, ry, vx, vy = x0, y0, vx0, vy0
+    rc, rs, fc, fs = np.cos(theta0), np.sin(theta0), 1.0, 0.0
+
+    def scaled(st):
+        rx_, ry_, vx_, vy_ = st[:4]
+        return [rx_ / rx_max, (ry_ - 0.5 * (ry_max + ry_min)) / (0.5 * (ry_max - ry_min)), vx_ / v_max,
+                vy_ / v_max] + list(st[4:])
+    z = scaled([rx, ry, vx, vy, rc, rs, fc, fs])
+    for Uk in U:
+        u = 0.5 * u_max * (np.asarray(Uk) + 1.0)
+        T = u[0] + u[1]
+        rx_n, ry_n = rx + dt * vx, ry + dt * vy
+        vx_n = vx - dt * T * rs / m
+        vy_n = vy + dt * (T * rc - m * g) / m
+        fs_n = fs + lever * dt * dt * (u[1] - u[0]) / inertia
+        fc_n = np.sqrt(1.0 - fs_n * fs_n)
+        rc_n, rs_n = rc * fc - rs * fs, rs * fc + rc * fs
+        rx, ry, vx, vy, rc, rs, fc, fs = rx_n, ry_n, vx_n, vy_n, rc_n, rs_n, fc_n, fs_n
+        z += list(Uk) + scaled([rx, ry, vx, vy, rc, rs, fc, fs])
+    return np.array(z)
+
+
+def test_paper_landing_lifting_feasible():
+    rng = np.random.default_rng(7)
+    p = wl.paper_landing_problem(N=4)
+    z = landing_rollout(rng.uniform(0.0, 0.6, size=(4, 2)))
+    sdp = R.relax(p)
+    X = R.lift_rank1(p, sdp, z)
+    assert np.max(np.abs(sdp.A @ X - sdp.b)) < 1e-12
+    assert abs(sdp.C @ X - p.objective(z)) < 1e-12 * (1 + abs(p.objective(z)))
+    for k, c in enumerate(p.cliques):
+        assert all(g.evaluate(p.clique_vars(z, k)) >= -1e-12 for g in c.g)
+    z[10 + 3] += 1e-4                  # v_y of x_1 (x_1 starts at z[10])
+    assert np.max(np.abs(sdp.A @ R.lift_rank1(p, sdp, z) - sdp.b)) > 1e-7
