@@ -124,7 +124,7 @@ def test_default_options_follow_the_same_readings_as_the_oracle(S):
         S.default_options(no_such_option=1)
 
 
-@pytest.mark.parametrize("model", ["landing", "flying"])
+@pytest.mark.parametrize("model", ["landing", "flying", "car"])
 def test_builder_on_the_paper_robots(S, model):
     """18- and 20-variable cliques (monomial keys of 3 bits per variable):
     bit-exact parity with the oracle at N = 3, Table 1's sizes at the paper's

@@ -286,10 +286,11 @@ def paper_robot_sizes():
     return out
 
 
-PAPER_ROBOTS = {"landing": "paper_landing_problem", "flying": "paper_flying_robot_problem"}
+PAPER_ROBOTS = {"landing": "paper_landing_problem", "flying": "paper_flying_robot_problem",
+                "car": "paper_car_backin_problem"}
 
 
-@pytest.mark.parametrize("model", ["landing", "flying"])
+@pytest.mark.parametrize("model", ["landing", "flying", "car"])
 def test_paper_robot_sizes(model):
     """Under the equality reading of the paper's pendulum (circles of x_{k-1}
     in cliques k >= 2, x_0 fixed by linear equalities) and with the printed
@@ -297,7 +298,10 @@ def test_paper_robot_sizes(model):
     model's Table 1 row, m included."""
     want = paper_robot_sizes()[model]
     p = getattr(wl, PAPER_ROBOTS[model])()
-    assert (p.dx, p.du) == (want["dx"][0], want["du"][0])
+    if "dx" in want:
+        assert (p.dx, p.du) == (want["dx"][0], want["du"][0])
+    else:
+        assert p.nv == want["nvars"][0], want["nvars"][1]
     sdp = R.relax(p)
     M = [b for b in sdp.blocks if b.kind == "M"]
     L = [b for b in sdp.blocks if b.kind == "L"]
@@ -383,4 +387,38 @@ def test_paper_landing_lifting_feasible():
     for k, c in enumerate(p.cliques):
         assert all(g.evaluate(p.clique_vars(z, k)) >= -1e-12 for g in c.g)
     z[10 + 3] += 1e-4                  # v_y of x_1 (x_1 starts at z[10])
+    assert np.max(np.abs(sdp.A @ R.lift_rank1(p, sdp, z) - sdp.b)) > 1e-7
+
+
+def car_rollout(V, Wr, dt=0.25, x0=2.0, y0=4.0, theta0=0.0, v_max=4.0, w_max=0.5, rx_max=4.0, ry_max=8.0):
+    """Explicit simulation of the car (unicycle with the third-order rotation
+    of the appendix), with the horizontal separating line y = 2 for both
+    obstacles (positions divided by 8, (A, B, C) normalised)."""
+    rx, ry, rc, rs = x0, y0, np.cos(theta0), np.sin(theta0)
+    line = np.array([0.0, 1.0, -0.25]) / np.sqrt(1.0625)
+    z = [rx / rx_max, ry / ry_max, rc, rs]
+    for Vk, Wk in zip(V, Wr):
+        v, w = v_max * Vk, w_max * Wk
+        fs = dt * w - (dt * w) ** 3 / 6.0
+        fc = np.sqrt(1.0 - fs * fs)
+        rx, ry = rx + dt * v * rc, ry + dt * v * rs
+        rc, rs = rc * fc - rs * fs, rs * fc + rc * fs
+        z += [Vk, Wk, fc, fs] + list(line) + list(line) + [rx / rx_max, ry / ry_max, rc, rs]
+    return np.array(z)
+
+
+def test_paper_car_backin_lifting_feasible():
+    """A rollout of the car with valid separating lines: every row of the SDP
+    holds at its rank-1 lifting, every inequality (corners on either side of
+    the lines, boxes) holds along it, and a perturbed position breaks it."""
+    rng = np.random.default_rng(8)
+    p = wl.paper_car_backin_problem(N=3)
+    z = car_rollout(rng.uniform(-0.3, 0.3, 3), rng.uniform(-0.5, 0.5, 3))
+    sdp = R.relax(p)
+    X = R.lift_rank1(p, sdp, z)
+    assert np.max(np.abs(sdp.A @ X - sdp.b)) < 1e-12
+    assert abs(sdp.C @ X - p.objective(z)) < 1e-12 * (1 + abs(p.objective(z)))
+    for k, c in enumerate(p.cliques):
+        assert all(g.evaluate(p.clique_vars(z, k)) >= -1e-12 for g in c.g)
+    z[14] += 1e-4                      # r_x of x_1 (x_1 starts at z[14])
     assert np.max(np.abs(sdp.A @ R.lift_rank1(p, sdp, z) - sdp.b)) > 1e-7

@@ -464,3 +464,79 @@ def paper_flying_robot_problem(N: int = 60, dt: float = 0.2, theta0: float = 0.3
     extra = _spread_previous_state_bounds(N, _extra_count(N, n_localizing, listed=9, N_paper=60, printed=659))
     return _so2_robot(N, 4, dt, theta0, thetadot0, x0, y0, vx0, vy0, box, u_max, fc_min,
                       (0.0, 0.0, 0.0, 0.0, 1.0, 0.0, 1.0, 0.0), Pf, dyn, extra, "paper_flying_robot")
+
+
+def paper_car_backin_problem(N: int = 30, dt: float = 0.25, x0: float = 2.0, y0: float = 4.0, theta0: float = 0.0,
+                             car_L: float = 6.0, car_W: float = 2.5, ry_max: float = 8.0, v_max: float = 4.0,
+                             w_max: float = 0.5, obstacles=((6.0, -4.0), (-6.0, -4.0)), side: float = 8.0,
+                             goal=(0.0, -3.0, 0.5 * np.pi), Pf: float = 10.0,
+                             n_localizing: int | None = None) -> Problem:
+    """The car back-in of the paper's appendix: a car (rectangle car_L x car_W)
+    backs in between two square obstacles, kept apart from each by a
+    separating line (A, B, C) with A^2 + B^2 + C^2 = 1 per step.
+
+    State x = (r_x, r_y, r_c, r_s); per step the clique-local variables
+    (v, w, f_c, f_s, A_1, B_1, C_1, A_2, B_2, C_2) play the part of the
+    control (the separating lines of one step are used by one clique only),
+    so cliques have 2 * 4 + 10 = 18 variables (moment blocks s(18, 2) = 190,
+    localizing blocks 19). Equalities of clique k: r_k = r_{k-1} + dt v
+    (r_c, r_s)_{k-1}; f_s = dt w - (dt w)^3 / 6; (r_c, r_s)_k = (r_c, r_s)_{k-1}
+    rotated by (f_c, f_s); the circles of (r_c, r_s)_k and (f_c, f_s), the two
+    unit spheres of the lines, the circle of (r_c, r_s)_{k-1} for k >= 2, and
+    x_0 fixed by four linear equalities in clique 1. Inequalities of clique
+    k: the four corners of the car at x_k on the positive side of each line
+    and the four corners of the matching obstacle on the other (16), and the
+    boxes of r_x,k, r_y,k, v, w (4): 20 per clique, 600 for N = 30, against
+    the 659 localizing matrices the appendix states; the other 59 are read as
+    bounds on the previous state. With N = 30 the SDP has Table 1's m.
+    """
+    dx, du = 4, 10
+    nv = 2 * dx + du
+    Vv = [Poly.var(nv, i) for i in range(nv)]
+    X0, Uv, X1 = Vv[:dx], Vv[dx:dx + du], Vv[dx + du:]
+    rx_max = x0 + 2.0
+    sx = (rx_max, ry_max)
+
+    def pos(X):
+        return X[0] * sx[0], X[1] * sx[1], X[2], X[3]
+    rx0, ry0, rc0, rs0 = pos(X0)
+    rx1, ry1, rc1, rs1 = pos(X1)
+    v, w, fc, fs = Uv[0] * v_max, Uv[1] * w_max, Uv[2], Uv[3]
+    lines = [(Uv[4], Uv[5], Uv[6]), (Uv[7], Uv[8], Uv[9])]
+    hx, hy = 0.5 * car_L, 0.5 * car_W
+    corners = [(rx1 + hx * rc1 - hy * rs1, ry1 + hx * rs1 + hy * rc1),
+               (rx1 - hx * rc1 - hy * rs1, ry1 - hx * rs1 + hy * rc1),
+               (rx1 - hx * rc1 + hy * rs1, ry1 - hx * rs1 - hy * rc1),
+               (rx1 + hx * rc1 + hy * rs1, ry1 + hx * rs1 - hy * rc1)]
+    # the lines act on positions divided by a common length so that their
+    # coefficients stay of order one after rescaling
+    ell = max(rx_max, ry_max)
+    g_target = [goal[0] / sx[0], goal[1] / sx[1], np.cos(goal[2]), np.sin(goal[2])]
+    n_extra = _extra_count(N, n_localizing, listed=20, N_paper=30, printed=659)
+    extra = _spread_previous_state_bounds(N, n_extra) if N >= 2 else (lambda k, X: [])
+    raw = []
+    for k in range(1, N + 1):
+        f = sum((xi - t) * (xi - t) for xi, t in zip(X0, g_target)) + sum(Uv[i] * Uv[i] for i in range(4))
+        if k == N:
+            f = f + Pf * sum((xi - t) * (xi - t) for xi, t in zip(X1, g_target))
+        h = [rx1 - rx0 - dt * v * rc0, ry1 - ry0 - dt * v * rs0, fs - dt * w + (dt * w) ** 3 * (1.0 / 6.0),
+             rc1 - (rc0 * fc - rs0 * fs), rs1 - (rs0 * fc + rc0 * fs), rc1 * rc1 + rs1 * rs1 - 1.0,
+             fc * fc + fs * fs - 1.0]
+        h += [A * A + B * B + C * C - 1.0 for A, B, C in lines]
+        if k >= 2:
+            h += [rc0 * rc0 + rs0 * rs0 - 1.0]
+        else:
+            h += [X0[0] - x0 / sx[0], X0[1] - y0 / sx[1], X0[2] - np.cos(theta0), X0[3] - np.sin(theta0)]
+        gg = []
+        for (A, B, C), (ox, oy) in zip(lines, obstacles):
+            gg += [A * (cx * (1.0 / ell)) + B * (cy * (1.0 / ell)) + C for cx, cy in corners]
+            s2 = 0.5 * side
+            for qx, qy in ((ox + s2, oy + s2), (ox - s2, oy + s2), (ox - s2, oy - s2), (ox + s2, oy - s2)):
+                gg.append(-(A * (qx / ell) + B * (qy / ell) + C))
+        gg += [1.0 - X1[0] * X1[0], 1.0 - X1[1] * X1[1], 1.0 - Uv[0] * Uv[0], 1.0 - Uv[1] * Uv[1]]
+        gg += extra(k, X0 + [X0[0]] * 4)
+        raw.append((f, gg, h))
+    fscale = 1.0 / max(f.max_abs_coef() for f, _, _ in raw)
+    cl = [Clique(f * fscale, [p.normalized() for p in gg], [p.normalized() for p in h]) for f, gg, h in raw]
+    return Problem("paper_car_backin", N, dx, du, cl, R=1.0, meta=dict(dt=dt, x0=x0, y0=y0, theta0=theta0,
+                                                                       fscale=fscale))
