@@ -390,7 +390,7 @@ def _spread_previous_state_bounds(N, total):
         counts[2 + j % (N - 1)] += 1
 
     def extra(k, X0):
-        return [1.0 - X0[j % 8] * X0[j % 8] for j in range(counts[k])]
+        return [1.0 - X0[j % len(X0)] * X0[j % len(X0)] for j in range(counts[k])]
     return extra
 
 
@@ -534,7 +534,7 @@ def paper_car_backin_problem(N: int = 30, dt: float = 0.25, x0: float = 2.0, y0:
             for qx, qy in ((ox + s2, oy + s2), (ox - s2, oy + s2), (ox - s2, oy - s2), (ox + s2, oy - s2)):
                 gg.append(-(A * (qx / ell) + B * (qy / ell) + C))
         gg += [1.0 - X1[0] * X1[0], 1.0 - X1[1] * X1[1], 1.0 - Uv[0] * Uv[0], 1.0 - Uv[1] * Uv[1]]
-        gg += extra(k, X0 + [X0[0]] * 4)
+        gg += extra(k, X0)
         raw.append((f, gg, h))
     fscale = 1.0 / max(f.max_abs_coef() for f, _, _ in raw)
     cl = [Clique(f * fscale, [p.normalized() for p in gg], [p.normalized() for p in h]) for f, gg, h in raw]
