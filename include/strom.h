@@ -311,7 +311,8 @@ void strom_transfer_bytes(uint64_t* h2d, uint64_t* d2h);
  *     rank 1; zbar (nullable, [nv]) receives the degree-1 entries of that
  *     submatrix's top eigenvector scaled to a leading 1 (NaN for variables
  *     not selected).
- * Errors: INVALID (bad sizes, non-finite or non-symmetric M). */
+ * nv in 1..21 (the cliques the builder takes). Errors: INVALID (bad sizes,
+ * non-finite or non-symmetric M). */
 typedef struct {
   int32_t n, rank, rank_low, flat, n_sub;
   double ratio_sub, lambda_max;

@@ -86,7 +86,7 @@ std::vector<double> principal(const double* M, int n, const std::vector<int>& id
 
 extern "C" int strom_moment_rank_test(const double* M, int32_t nv, const uint8_t* vars, double tol,
                                       strom_rank_test* out, double* zbar) {
-  if (!M || !out || nv < 1 || nv > 16 || !(tol > 0.0) || !std::isfinite(tol)) {
+  if (!M || !out || nv < 1 || nv > 21 || !(tol > 0.0) || !std::isfinite(tol)) {
     strom::set_error("strom_moment_rank_test: bad arguments");
     return STROM_ERR_INVALID;
   }

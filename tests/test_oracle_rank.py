@@ -108,3 +108,25 @@ def test_library_rejects_bad_input(S):
         S.moment_rank_test(bad, 2)
     with pytest.raises(ValueError):
         S.moment_rank_test(M, 3)
+
+
+def test_partial_rank_one_on_the_paper_car_backin_clique(S):
+    """The car back-in's extraction: a clique of 18 variables (attitude and
+    inputs of two steps, plus six separating-line variables) whose moments
+    come from two trajectories that agree on the trajectory variables but use
+    different separating lines. M_k (190 x 190) has rank 2; the submatrix on
+    the trajectory variables has rank 1 and yields them; library == oracle."""
+    rng = np.random.default_rng(9)
+    nv = 18
+    traj = np.ones(nv, bool)
+    traj[8:14] = False                         # (x_{k-1} 4, v w f_c f_s, lines 6, x_k 4): the lines
+    z1 = rng.uniform(-0.9, 0.9, nv)
+    z2 = z1.copy()
+    z2[~traj] = rng.uniform(-0.9, 0.9, (~traj).sum())
+    M = _moments([z1, z2], [0.55, 0.45])
+    want_full, want_part = OC.moment_rank_tests(M, nv), OC.moment_rank_tests(M, nv, traj)
+    assert want_full["n"] == 190 and want_full["rank"] == 2 and want_full["ratio_sub"] > 1e-3
+    assert abs(want_part["ratio_sub"]) < 1e-12
+    assert np.allclose(want_part["zbar_sub"][traj], z1[traj], atol=1e-10)
+    _same(S.moment_rank_test(M, nv), want_full)
+    _same(S.moment_rank_test(M, nv, traj), want_part)
