@@ -151,6 +151,23 @@ def test_builder_on_the_paper_robots(S, model):
         S.Solver([S.Problem(small).relax()])
 
 
+def test_binding_constants_match_the_header():
+    """The Python constants are the values strom.h defines (status codes,
+    precision modes, the warm-start key limit), and the oracle's row kinds
+    are the header's STROM_ROW_* numbering."""
+    import re
+    from paper_2406_05846_gb300 import _native as N
+    text = open(os.path.join(ROOT, "include", "strom.h")).read()
+    vals = {k: int(v) for k, v in re.findall(r"\b(STROM_[A-Z0-9_]+)\s*=\s*(-?\d+)", text)}
+    vals.update({k: int(v) for k, v in re.findall(r"#define\s+(STROM_[A-Z0-9_]+)\s+(\d+)", text)})
+    for k in ("STROM_OK", "STROM_MAXITER", "STROM_PENDING", "STROM_PREC_FP64", "STROM_PREC_FP32",
+              "STROM_PREC_MIXED", "STROM_WARM_MAX_KEY"):
+        assert getattr(N, k) == vals[k], k
+    assert (OR.KIND_MOM, OR.KIND_INEQ, OR.KIND_EQ, OR.KIND_PHI0, OR.KIND_CONS) == \
+        (vals["STROM_ROW_MOM"], vals["STROM_ROW_INEQ"], vals["STROM_ROW_EQ"], vals["STROM_ROW_PHI0"],
+         vals["STROM_ROW_CONS"])
+
+
 def test_problem_validation(S):
     p = wl.toy_problem(N=2)
     p.kappa = 3
