@@ -470,14 +470,18 @@ int strom_kernel_psd_project(const double* Xb_dev, const int64_t* blk_off, const
  * framework that owns the whole device pool, a real-time loop that must not
  * allocate after start-up). It allocates nothing: the block table and the
  * FP64 eigenvector scratch live in a static device array of the library
- * (about 4.4 MB, held by every GPU that loads the library until exit).
+ * (about 4.37 MB, held by every GPU that loads the library until exit).
  * The paper has no counterpart; this is a deployment variant.
  * Limits: nblk <= 65536 (else STROM_ERR_INVALID, nothing launched); block
- * sizes 1..160. The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) and caches it: make that call before any
- * stream capture. All calls share the array, so calls that overlap on the
- * GPU race; the caller serialises them. The call returns after the stream
- * has finished the projection. blk_off / blk_n are host arrays. */
+ * sizes 1..160. Set-up: the first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress), caches it and loads the kernels it
+ * launches; under CUDA's lazy module loading that loading is when the static
+ * array and the kernels' code take their device memory. A call with nblk = 0
+ * (all pointers may then be NULL) does the set-up alone: a caller that must
+ * not allocate later makes it at start-up, before any stream capture.
+ * All calls share the array, so calls that overlap on the GPU race; the
+ * caller serialises them. Every call synchronises `stream` and returns after
+ * the projection has finished. blk_off / blk_n are host arrays. */
 int strom_kernel_psd_project_noalloc(const double* Xb_dev, const int64_t* blk_off, const int32_t* blk_n,
                                      int32_t nblk, int32_t precision, double* P_dev, void* stream);
 

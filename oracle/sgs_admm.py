@@ -7,7 +7,9 @@ Everything here is plain FP64 NumPy/SciPy:
                      as scipy sparse products in svec coordinates;
   * reduce_rows      removal of linearly dependent rows so that A A^* > 0,
                      decided by a pivot-skipping Cholesky in a fixed order
-                     (cliques N..1, natural row order inside a clique);
+                     (cliques N..1, natural row order inside a clique), on
+                     the Gram matrix of the rows other than A_mom after
+                     projecting out span(A_mom) (other_rows_gram);
   * YSolver          y = (A A^*)^{-1} r with a sparse LU of A A^* (library);
   * solve            Steps 1-4 of Algorithm 1 and the terminal conditions
                      of eq. (kkt-residual).
@@ -25,9 +27,10 @@ from dataclasses import dataclass, field
 
 import numpy as np
 import scipy.sparse as sp
+import scipy.sparse.csgraph  # noqa: F401  (sp.csgraph)
 import scipy.sparse.linalg as spla
 
-from .relax import KIND_MOM, SDP, smat, svec
+from .relax import KIND_CONS, KIND_MOM, SDP, smat, svec
 
 RANK_TOL = 1e-8
 
@@ -75,6 +78,47 @@ def canonical_row_order(sdp: SDP) -> np.ndarray:
     return np.concatenate([idx[sdp.row_clique == k] for k in range(sdp.N - 1, -1, -1)])
 
 
+def other_rows_gram(sdp: SDP):
+    """Gram matrix of the rows other than A_mom after projecting out span(A_mom).
+
+    With A_s the A_mom rows and A_o the others, the projection of A_o on the
+    orthogonal complement of the row space of A_s has the Gram matrix
+        S = A_o A_o^T - (A_s A_o^T)^T (A_s A_s^T)^{-1} (A_s A_o^T),
+    formed here with sparse products and a sparse solve (A_s A_s^T is block
+    diagonal: one block per monomial with duplicate entries). Returns S
+    (sparse, rows and columns in the natural order of the other rows) and
+    the row ids of those rows.
+    """
+    A = sdp.A.tocsr()
+    is_s = sdp.row_kind == KIND_MOM
+    As, Ao = A[is_s], A[~is_s]
+    other_rows = np.nonzero(~is_s)[0]
+    if As.shape[0] == 0:
+        return (Ao @ Ao.T).tocsr(), other_rows
+    Gs = (As @ As.T).tocsr()
+    B = (As @ Ao.T).tocsc()
+    S = (Ao @ Ao.T) - (B.T @ block_diagonal_inverse(Gs) @ B)
+    return sp.csr_matrix(S), other_rows
+
+
+def block_diagonal_inverse(G: sp.csr_matrix) -> sp.csr_matrix:
+    """Inverse of a symmetric positive definite block-diagonal sparse matrix
+    whose blocks are small (the connected components of its graph), each
+    block inverted densely."""
+    ncomp, lab = sp.csgraph.connected_components(G, directed=False)
+    order = np.argsort(lab, kind="stable")
+    bounds = np.searchsorted(lab[order], np.arange(ncomp + 1))
+    rows, cols, vals = [], [], []
+    for c in range(ncomp):
+        ids = order[bounds[c]:bounds[c + 1]]
+        inv = np.linalg.inv(G[ids][:, ids].toarray())
+        rows.append(np.repeat(ids, len(ids)))
+        cols.append(np.tile(ids, len(ids)))
+        vals.append(inv.ravel())
+    n = G.shape[0]
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+
+
 def reduce_rows(sdp: SDP, tol: float = RANK_TOL):
     """Boolean keep-mask over the rows of A and the relative pivots.
 
@@ -84,41 +128,59 @@ def reduce_rows(sdp: SDP, tol: float = RANK_TOL):
     entry no other row touches, so they are always independent; and a row of
     clique k shares no entry with the A_mom rows of any other clique.
     Hence the test may run on the other rows after projecting out the span
-    of all A_mom rows, which is what is done here.
+    of all A_mom rows (Gram matrix S of other_rows_gram).
+
+    The pivot-skipping Cholesky of S runs in the canonical order (cliques
+    N..1, natural row order inside a clique). In that order S is block
+    tridiagonal: the rows of clique k meet only each other and the consensus
+    rows of clique k-1 (the one kind of row of clique k-1 that touches M_k).
+    So the elimination of clique k's rows is carried out on a dense window
+    holding those rows and the consensus rows of clique k-1; what it
+    subtracts from the consensus rows' Gram is carried to clique k-1's
+    window. This is the same scalar algorithm on the same matrix, entry by
+    entry, without storing the zero blocks.
     """
-    A = sdp.A.tocsr()
-    is_s = sdp.row_kind == KIND_MOM
-    As, Ao = A[is_s], A[~is_s]
-    Gs = (As @ As.T).tocsc()
-    lu = spla.splu(Gs)
-    Z = lu.solve((As @ Ao.T).toarray())             # (As As^T)^{-1} As Ao^T
-    Ahat = Ao.toarray() - (As.T @ Z).T              # Ao minus its projection on span(As)
-    other_rows = np.nonzero(~is_s)[0]
-    order_all = canonical_row_order(sdp)
-    pos = {r: i for i, r in enumerate(other_rows)}
-    order = np.array([pos[r] for r in order_all if not is_s[r]])
-    G = Ahat[order] @ Ahat[order].T
-    m = len(order)
-    keep_o = np.zeros(m, dtype=bool)
-    rel = np.zeros(m)
-    for i in range(m):
-        d = G[i, i]
-        nrm = np.dot(Ahat[order[i]], Ahat[order[i]])
-        rel[i] = d / nrm if nrm > 0 else 0.0
-        if nrm <= 0 or d <= tol * nrm:
-            G[i, i + 1:] = 0.0
-            G[i + 1:, i] = 0.0
-            continue
-        keep_o[i] = True
-        l = G[i + 1:, i] / np.sqrt(d)
-        nz = np.nonzero(l)[0]
-        if len(nz):
-            sub = i + 1 + nz
-            G[np.ix_(sub, sub)] -= np.outer(l[nz], l[nz])
-    keep = is_s.copy()
-    keep[other_rows[order[keep_o]]] = True
+    S, other_rows = other_rows_gram(sdp)
+    S = S.tocsr()
+    rc = sdp.row_clique[other_rows]
+    rk = sdp.row_kind[other_rows]
+    keep_o = np.zeros(len(other_rows), dtype=bool)
+    rel_o = np.zeros(len(other_rows))
+    carry = None          # Schur update waiting for the consensus rows of the clique below
+    for k in range(sdp.N - 1, -1, -1):
+        G = np.nonzero(rc == k)[0]                                   # natural order
+        P = np.nonzero((rc == k - 1) & (rk == KIND_CONS))[0] if k > 0 else np.zeros(0, int)
+        idx = np.concatenate([G, P])
+        W = S[idx][:, idx].toarray()
+        nG = len(G)
+        W[nG:, nG:] = 0.0                      # the consensus rows' own Gram enters in their window
+        if carry is not None:
+            cons = np.nonzero(rk[G] == KIND_CONS)[0]
+            W[np.ix_(cons, cons)] -= carry
+        d0 = np.array(S[G, G]).ravel()         # squared norms of the projected rows
+        for j in range(nG):
+            d = W[j, j]
+            rel_o[G[j]] = d / d0[j] if d0[j] > 0 else 0.0
+            if d0[j] <= 0 or d <= tol * d0[j]:
+                W[j, j + 1:] = 0.0
+                W[j + 1:, j] = 0.0
+                continue
+            keep_o[G[j]] = True
+            l = W[j + 1:, j] / np.sqrt(d)
+            nz = np.nonzero(l)[0]
+            if len(nz):
+                lo, hi = nz[0], nz[-1] + 1
+                if 2 * len(nz) >= hi - lo:      # dense enough: update the whole range (zeros change nothing)
+                    W[j + 1 + lo:j + 1 + hi, j + 1 + lo:j + 1 + hi] -= np.outer(l[lo:hi], l[lo:hi])
+                else:
+                    sub = j + 1 + nz
+                    W[np.ix_(sub, sub)] -= np.outer(l[nz], l[nz])
+        carry = -W[nG:, nG:] if len(P) else None
+    keep = sdp.row_kind == KIND_MOM
+    keep = keep.copy()
+    keep[other_rows[keep_o]] = True
     rel_full = np.ones(sdp.m)
-    rel_full[other_rows[order]] = rel
+    rel_full[other_rows] = rel_o
     return keep, rel_full
 
 

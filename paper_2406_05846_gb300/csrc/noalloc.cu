@@ -7,12 +7,17 @@
 // PSD projection with no device (or host heap) allocation: the block table
 // and the FP64 eigenvector scratch live in one file-scope static __device__
 // array, g_noalloc, which every GPU that loads the library holds until the
-// process exits (about 4.4 MB).
+// process exits (about 4.37 MB).
 //
 // Host code never names g_noalloc as if it were a device address (in host
 // code the name is only a host-side stand-in). Its device address is taken
 // once per device with cudaGetSymbolAddress, on the first call made with that
 // device current, and cached; make that first call before any stream capture.
+// Under CUDA's lazy module loading the device code of this file and of the
+// projection kernels, and with it g_noalloc itself, is loaded into device
+// memory on first use; the set-up therefore also forces the loading of every
+// kernel the entry point launches. A call with nblk = 0 does only this
+// set-up, so a caller that must not allocate later makes it at start-up.
 // Every call reuses the same array, which keeps the previous call's contents:
 // calls that overlap on the GPU (different streams, or different host threads
 // on one device) race and must be serialised by the caller.
@@ -32,7 +37,6 @@ constexpr int kMaxDevices = 64;
 
 struct NoAllocScratch {
   int64_t off[kNoAllocMaxBlocks];
-  int64_t lam_off[kNoAllocMaxBlocks];
   int32_t n[kNoAllocMaxBlocks];
   int32_t list[kNoAllocMaxBlocks];
   int32_t fill[4];
@@ -45,23 +49,10 @@ static __device__ __align__(256) NoAllocScratch g_noalloc;
 std::mutex g_mu;
 NoAllocScratch* g_addr[kMaxDevices] = {};
 
-NoAllocScratch* scratch_for_current_device() {
-  int dev = 0;
-  STROM_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) throw StatusError(STROM_ERR_INVALID, "device index out of range");
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (g_addr[dev] == nullptr) {
-    void* p = nullptr;
-    STROM_CUDA(cudaGetSymbolAddress(&p, g_noalloc));
-    g_addr[dev] = static_cast<NoAllocScratch*>(p);
-  }
-  return g_addr[dev];
-}
-
 __device__ __forceinline__ int size_class(int n) { return n <= 16 ? 0 : n <= 40 ? 1 : n <= 80 ? 2 : 3; }
 
 // counting sort of the blocks by size class (order inside a class does not
-// matter: every block is projected independently) and eigenvalue offsets
+// matter: every block is projected independently)
 __global__ void __launch_bounds__(1024) classify_kernel(NoAllocScratch* sc, int nblk) {
   __shared__ int cnt[4], start[4];
   if (threadIdx.x < 4) cnt[threadIdx.x] = 0;
@@ -85,6 +76,25 @@ __global__ void __launch_bounds__(1024) classify_kernel(NoAllocScratch* sc, int 
   }
 }
 
+// set-up of the current device, once: the device address of g_noalloc, the
+// projection kernels' attributes, and the loading of classify_kernel (the
+// attribute queries load each kernel's module under lazy loading)
+NoAllocScratch* scratch_for_current_device() {
+  int dev = 0;
+  STROM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) throw StatusError(STROM_ERR_INVALID, "device index out of range");
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_addr[dev] == nullptr) {
+    void* p = nullptr;
+    STROM_CUDA(cudaGetSymbolAddress(&p, g_noalloc));
+    psd_configure();
+    cudaFuncAttributes fa;
+    STROM_CUDA(cudaFuncGetAttributes(&fa, classify_kernel));
+    g_addr[dev] = static_cast<NoAllocScratch*>(p);
+  }
+  return g_addr[dev];
+}
+
 }  // namespace
 }  // namespace strom
 
@@ -92,7 +102,7 @@ extern "C" int strom_kernel_psd_project_noalloc(const double* Xb_dev, const int6
                                                 int32_t nblk, int32_t precision, double* P_dev, void* stream) {
   using namespace strom;
   try {
-    if (!Xb_dev || !P_dev || Xb_dev == P_dev || nblk < 0 || (nblk > 0 && (!blk_off || !blk_n)))
+    if (nblk < 0 || (nblk > 0 && (!Xb_dev || !P_dev || Xb_dev == P_dev || !blk_off || !blk_n)))
       throw StatusError(STROM_ERR_INVALID, "strom_kernel_psd_project_noalloc: bad arguments");
     if (nblk > kNoAllocMaxBlocks)
       throw StatusError(STROM_ERR_INVALID,
@@ -102,10 +112,9 @@ extern "C" int strom_kernel_psd_project_noalloc(const double* Xb_dev, const int6
     for (int i = 0; i < nblk; ++i)
       if (blk_n[i] < 1 || blk_n[i] > 160 || blk_off[i] < 0)
         throw StatusError(STROM_ERR_INVALID, "strom_kernel_psd_project_noalloc: block size must be in 1..160");
+    NoAllocScratch* sc = scratch_for_current_device();
     if (nblk == 0) return STROM_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    NoAllocScratch* sc = scratch_for_current_device();
-    psd_configure();
     STROM_CUDA(cudaMemcpyAsync(sc->off, blk_off, sizeof(int64_t) * nblk, cudaMemcpyHostToDevice, st));
     STROM_CUDA(cudaMemcpyAsync(sc->n, blk_n, sizeof(int32_t) * nblk, cudaMemcpyHostToDevice, st));
     classify_kernel<<<1, 1024, 0, st>>>(sc, nblk);
@@ -120,7 +129,7 @@ extern "C" int strom_kernel_psd_project_noalloc(const double* Xb_dev, const int6
     a.blk_off = sc->off;
     a.blk_n = sc->n;
     a.blk_list = sc->list;
-    a.lam_off = sc->lam_off;
+    a.lam_off = nullptr;  // no eigenvalue output: the kernels read lam_off only with lam or topvec
     a.vscratch = sc->vs;
     // FP64 blocks of the largest class keep V in the static scratch: run them
     // in chunks of at most kNoAllocMaxVBlocks, in stream order

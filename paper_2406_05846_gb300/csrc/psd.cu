@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -381,9 +382,17 @@ void launch_class(const PsdArgs& a, int start, int count, double tol, int sweeps
 
 }  // namespace
 
+// The shared-memory attributes are per device: each device is configured once,
+// under a lock so that host threads calling at the same time do not race.
 void psd_configure() {
-  static bool done = false;
-  if (done) return;
+  constexpr int kMaxDev = 64;
+  static std::mutex mu;
+  static bool done[kMaxDev] = {};
+  int dev = 0;
+  STROM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDev) throw StatusError(STROM_ERR_INVALID, "psd_configure: device index out of range");
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return;
   set_attr<double, 16, 64, true>();
   set_attr<double, 40, 128, true>();
   set_attr<double, 80, 256, true>();
@@ -392,7 +401,7 @@ void psd_configure() {
   set_attr<float, 40, 128, true>();
   set_attr<float, 80, 256, true>();
   set_attr<float, 160, 512, true>();
-  done = true;
+  done[dev] = true;
 }
 
 void psd_launch(const PsdArgs& a, const PsdClasses& c, int precision, cudaStream_t st) {

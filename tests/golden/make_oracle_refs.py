@@ -1,0 +1,91 @@
+"""Writes tests/golden/oracle_refs.json: the FP64 oracle's reference solves of
+the seeded instances that the whole-solve GPU parity tests compare against.
+
+Each reference is Algorithm 1 of the oracle (oracle/sgs_admm.py) run to
+max(eta_p, eta_d, eta_g) <= 1e-8 (the objective parity of a GPU solve at
+1e-6 is judged against it), followed by the oracle's certificate
+(oracle/certify.py: rank-1 test, extraction, rollout, lower bound, xi) at
+that solution. Only oracle/ computes; workloads/ supplies the seeded inputs.
+
+Sets (instance i of a set is workloads.problem_batch(kind, ...)[i]):
+  pendulum    N = 10, seeds 0..7 of the pendulum batch
+  cartpole    N = 50, seeds 0..7 of the cart-pole batch
+  rigid_body  the 8 instances of the 128-instance uneven batch
+              (N ~ U{20..100}) with the shortest horizons
+
+Usage: python tests/golden/make_oracle_refs.py SET [SET ...] [--workers K]
+Existing entries of other sets are kept. Single-threaded BLAS per worker.
+"""
+from __future__ import annotations
+
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+OUT = os.path.join(HERE, "oracle_refs.json")
+
+RIGID_BATCH = 128
+TOL = 1e-8
+MAXITER = 60000
+
+
+def instances(kind):
+    sys.path.insert(0, ROOT)
+    import workloads as wl
+    if kind == "pendulum":
+        ps = wl.problem_batch("pendulum", 8, N=10)
+        return [(i, p) for i, p in enumerate(ps)]
+    if kind == "cartpole":
+        ps = wl.problem_batch("cartpole", 8, N=50)
+        return [(i, p) for i, p in enumerate(ps)]
+    if kind == "rigid_body":
+        ps = wl.problem_batch("rigid_body", RIGID_BATCH)
+        order = sorted(range(len(ps)), key=lambda i: (ps[i].N, i))[:8]
+        return [(i, ps[i]) for i in sorted(order)]
+    raise ValueError(kind)
+
+
+def solve_one(args):
+    kind, i = args
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    sys.path.insert(0, ROOT)
+    from oracle import certify as OC
+    from oracle import relax as OR
+    from oracle import sgs_admm as OA
+    p = dict(instances(kind))[i]
+    t0 = time.time()
+    red = OA.reduce(OR.relax(p))
+    res = OA.solve(red, OA.Options(tol=TOL, maxiter=MAXITER))
+    c = OC.certify(p, red, res.X, res.y)
+    return {"kind": kind, "index": i, "N": p.N, "iterations": res.iters, "converged": bool(res.converged),
+            "pobj": res.pobj, "dobj": res.dobj, "eta": [res.eta_p, res.eta_d, res.eta_g],
+            "m_kept": int(red.keep.sum()), "max_ratio": c.max_ratio, "feasible": bool(c.feasible),
+            "rank_one": bool(c.rank_one), "certified": bool(c.certified), "lower_bound": c.lower_bound,
+            "phat": c.phat, "xi": c.xi, "seconds": time.time() - t0}
+
+
+def main(argv):
+    workers = 4
+    if "--workers" in argv:
+        k = argv.index("--workers")
+        workers = int(argv[k + 1])
+        argv = argv[:k] + argv[k + 2:]
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    jobs = [(kind, i) for kind in argv for i, _ in instances(kind)]
+    refs = json.load(open(OUT)) if os.path.exists(OUT) else {}
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(workers) as pool:
+        for r in pool.imap_unordered(solve_one, jobs):
+            refs.setdefault(r["kind"], {})[str(r["index"])] = r
+            with open(OUT + ".tmp", "w") as f:
+                json.dump(refs, f, indent=1, sort_keys=True)
+            os.replace(OUT + ".tmp", OUT)
+            print(json.dumps(r), flush=True)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:])

@@ -33,6 +33,29 @@ def test_reduction_rank_and_spd():
             assert np.max(np.abs(Ak.T @ coef - drop.T)) < 1e-9
 
 
+def test_reduction_is_greedy_in_canonical_order():
+    """The kept set is the greedy basis of the rows in the canonical order
+    (cliques N..1, natural order inside a clique): a row is dropped exactly
+    when it lies in the span of the rows before it. Checked with an
+    orthonormal basis of the kept rows grown by Gram-Schmidt (projected
+    twice), independently of the Cholesky used by reduce_rows."""
+    for p in (wl.toy_problem(N=3), wl.pendulum_problem(N=2, theta0=0.13)):
+        sdp = R.relax(p)
+        keep, _ = O.reduce_rows(sdp)
+        Ad = sdp.A.toarray()
+        Q = np.zeros((int(keep.sum()), Ad.shape[1]))
+        k = 0
+        for row in O.canonical_row_order(sdp):
+            a = Ad[row]
+            r = a - Q[:k].T @ (Q[:k] @ a)
+            r = r - Q[:k].T @ (Q[:k] @ r)
+            resid = np.linalg.norm(r) / np.linalg.norm(a)
+            assert (resid < 1e-6) == (not keep[row]), (p.name, row, resid)
+            if keep[row]:
+                Q[k] = r / np.linalg.norm(r)
+                k += 1
+
+
 def test_ysolver_backward_error():
     p = wl.pendulum_problem(N=4, theta0=0.05)
     red = O.reduce(R.relax(p))

@@ -64,3 +64,57 @@ def test_noalloc_rejects_too_many_blocks():
                                             C.c_void_p(out.data_ptr()), None)
     assert st == -1
     assert b"65536" in L.strom_last_error()
+
+
+_CHILD = r"""
+import ctypes as C, json, sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+sys.path.insert(0, sys.argv[1] + "/tests")
+import torch
+import workloads as wl
+from gpu_common import lib, svec_blocks
+torch.cuda.set_device(0)
+S = lib()
+L = S.lib()
+calls = []
+for seed, sizes in ((31, [8, 36, 78, 136, 136, 12]), (32, [160, 3, 41, 81])):
+    mats, _, _ = wl.known_spectrum_blocks(sizes, seed=seed)
+    x, off, n = svec_blocks(mats)
+    xb = torch.tensor(x, dtype=torch.float64, device="cuda:0")
+    calls.append((xb, torch.zeros_like(xb), np.ascontiguousarray(off, np.int64), np.ascontiguousarray(n, np.int32)))
+torch.cuda.synchronize()
+def run(xb, out, off, n, prec):
+    if xb is None:
+        return L.strom_kernel_psd_project_noalloc(None, None, None, 0, prec, None, None)
+    return L.strom_kernel_psd_project_noalloc(C.c_void_p(xb.data_ptr()), off.ctypes.data_as(C.POINTER(C.c_int64)),
+                                              n.ctypes.data_as(C.POINTER(C.c_int32)), len(n), prec,
+                                              C.c_void_p(out.data_ptr()), None)
+free = [torch.cuda.mem_get_info(0)[0]]
+st = [run(None, None, None, None, 0)]
+free.append(torch.cuda.mem_get_info(0)[0])
+for prec in (0, 1):
+    for c in calls:
+        st.append(run(*c, prec))
+        free.append(torch.cuda.mem_get_info(0)[0])
+print(json.dumps({"status": st, "free": free}))
+"""
+
+
+def test_noalloc_allocates_nothing_after_setup():
+    """In a fresh process where no library kernel has run yet: the set-up call
+    (nblk = 0) may take device memory (module loading of the kernels and of
+    the static array), every later call takes none."""
+    import json
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", _CHILD, root], capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-4000:]
+    rec = json.loads(out.stdout.strip().splitlines()[-1])
+    assert rec["status"] == [0] * 5, rec
+    free = rec["free"]
+    assert free[1] <= free[0]                          # set-up: module loading may take memory
+    assert all(f == free[1] for f in free[2:]), free   # later calls: not one byte
