@@ -36,6 +36,15 @@ enum {
   STROM_ERR_CUDA = -6         /* a CUDA runtime call failed */
 };
 
+/* factorisations of the y-solve's Schur complement (strom_options.factor).
+ * DENSE: one dense lower triangle per clique and a dense coupling block
+ * (blocked substitution through inverted 32 x 32 diagonal blocks); SPARSE:
+ * the sparse Cholesky factor of strom_sdp_factor_info (level-scheduled
+ * substitution). Both take the same pivot decisions in the same order and
+ * give the same y up to rounding. AUTO: DENSE when every clique group has
+ * at most 800 rows and the dense factor takes at most 8 GB, else SPARSE. */
+enum { STROM_FACTOR_AUTO = 0, STROM_FACTOR_DENSE = 1, STROM_FACTOR_SPARSE = 2 };
+
 /* precision modes of the PSD projection */
 enum {
   STROM_PREC_FP64 = 0,        /* Jacobi eigensolver in FP64 (plain) */
@@ -161,6 +170,26 @@ int strom_sdp_star_export(const strom_sdp* s, int64_t* nclass, int64_t* nstar, i
                           double* dsum, int32_t* ptr, int64_t* row, double* inv_s2, double* omega,
                           double* inv_rep_s);
 
+/* Size of the sparse factor the y-solve uses for this SDP (host only, no GPU
+ * needed). After the exact star elimination of the A_mom rows, the y-solve
+ * factorises the Gram S of the other rows (eq. cholesky on the reduced
+ * system) in the canonical order of the row reduction (cliques N..1, natural
+ * order inside a clique), where S is block tridiagonal by clique and its
+ * Cholesky factor L is block bidiagonal. Reported: the other rows (n_other;
+ * the last group, the first clique's, starts at n_tail), the strictly lower
+ * entries of S and of L (pattern without pivoting; dropped rows keep their
+ * zero entries), the dependent steps of the forward and backward solves
+ * (level schedules inside each clique's group, summed over groups), the
+ * largest group, the longest column of L, the largest row distance inside
+ * a column, and the entries of dense lower triangles of the groups (the
+ * storage a dense per-clique factor would need). Errors: INVALID when the
+ * rows are not chain-ordered. */
+typedef struct {
+  int64_t n_other, n_tail, nnz_S, nnz_L, dense_entries;
+  int32_t levels_fwd, levels_bwd, max_group, max_col, max_span;
+} strom_factor_info;
+int strom_sdp_factor_info(const strom_sdp* s, strom_factor_info* out);
+
 /* ------------------------------------------------------------------------
  * Solver: sGS-ADMM (Algorithm 1) on a batch of independent SDPs, all on the
  * current CUDA device. Creation uploads the data, removes linearly dependent
@@ -192,6 +221,7 @@ typedef struct {
                                 clique (e.g. one robot, different initial states), the factor of
                                 cliques 2..N is computed once and shared (cliques are eliminated
                                 N..1, so only the first clique's factor differs) */
+  int32_t factor;            /* STROM_FACTOR_*: how A A^T is factorised for the y-solve */
 } strom_options;
 
 void strom_options_default(strom_options* o);

@@ -9,6 +9,7 @@ LIB_PATH = os.path.join(HERE, "libstrom.so")
 
 STROM_OK, STROM_MAXITER, STROM_PENDING = 0, 1, 2
 STROM_PREC_FP64, STROM_PREC_FP32, STROM_PREC_MIXED = 0, 1, 2
+STROM_FACTOR_AUTO, STROM_FACTOR_DENSE, STROM_FACTOR_SPARSE = 0, 1, 2
 STROM_WARM_MAX_KEY = 8
 
 
@@ -46,7 +47,7 @@ class strom_options(C.Structure):
                 ("sigma_min", C.c_double), ("sigma_max", C.c_double), ("rank_tol", C.c_double),
                 ("precision", C.c_int32), ("polish_eta", C.c_double), ("check_every", C.c_int32),
                 ("time_budget_s", C.c_double), ("eig_warm_period", C.c_int32),
-                ("share_tail", C.c_int32)]
+                ("share_tail", C.c_int32), ("factor", C.c_int32)]
 
 
 class strom_result(C.Structure):
@@ -59,6 +60,12 @@ class strom_certificate(C.Structure):
     _fields_ = [("max_ratio", C.c_double), ("lower_bound", C.c_double), ("phat", C.c_double), ("xi", C.c_double),
                 ("hmax", C.c_double), ("gmin", C.c_double), ("feasible", C.c_int32), ("rank_one", C.c_int32),
                 ("certified", C.c_int32)]
+
+
+class strom_factor_info(C.Structure):
+    _fields_ = [("n_other", C.c_int64), ("n_tail", C.c_int64), ("nnz_S", C.c_int64), ("nnz_L", C.c_int64),
+                ("dense_entries", C.c_int64), ("levels_fwd", C.c_int32), ("levels_bwd", C.c_int32),
+                ("max_group", C.c_int32), ("max_col", C.c_int32), ("max_span", C.c_int32)]
 
 
 class strom_rank_test(C.Structure):
@@ -88,6 +95,7 @@ SIGNATURES = {
     "strom_sdp_export": (C.c_int, [P, PI32, PI64, PI8, PI32, PD, PI64, PI32, PD, PD, PI8, PI32]),
     "strom_sdp_destroy": (None, [P]),
     "strom_sdp_import": (C.c_int, [C.POINTER(strom_sdp_desc), C.POINTER(P)]),
+    "strom_sdp_factor_info": (C.c_int, [P, C.POINTER(strom_factor_info)]),
     "strom_sdp_star_export": (C.c_int, [P, PI64, PI64, PI64, PD, PD, PI32, PI64, PD, PD, PD]),
     "strom_options_default": (None, [C.POINTER(strom_options)]),
     "strom_solver_create": (C.c_int, [C.POINTER(P), C.c_int32, C.POINTER(strom_options), C.POINTER(P)]),

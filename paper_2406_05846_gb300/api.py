@@ -130,6 +130,12 @@ class Sdp:
               "strom_sdp_star_export")
         return o
 
+    def factor_info(self) -> dict:
+        """strom_sdp_factor_info: size of the y-solve's sparse factor for this SDP."""
+        fi = N.strom_factor_info()
+        check(lib().strom_sdp_factor_info(self.handle, C.byref(fi)), "strom_sdp_factor_info")
+        return {k: getattr(fi, k) for k, _ in fi._fields_}
+
     def __del__(self):
         if getattr(self, "handle", None):
             lib().strom_sdp_destroy(self.handle)

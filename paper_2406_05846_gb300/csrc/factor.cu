@@ -655,6 +655,20 @@ void ysolve_factor(const YsolveDev& d, int ngroups, int ninst, double rank_tol, 
   count_launches(1);
 }
 
+void ysolve_star_pre(const YsolveDev& d, const double* r, double* rho, cudaStream_t st) {
+  if (d.nclass == 0) return;
+  star_pre_kernel<<<ceil_div(d.nclass, 256), 256, 0, st>>>(d, r, rho);
+  STROM_CUDA(cudaGetLastError());
+  count_launches(1);
+}
+
+void ysolve_star_post(const YsolveDev& d, const double* r, double* y, cudaStream_t st) {
+  if (d.nclass == 0) return;
+  star_post_kernel<<<ceil_div(d.nclass, 256), 256, 0, st>>>(d, r, y);
+  STROM_CUDA(cudaGetLastError());
+  count_launches(1);
+}
+
 void ysolve_apply(const YsolveDev& d, int ninst, int max_group, const double* r, double* y, double* rho,
                   cudaStream_t st) {
   if (d.nclass > 0) {

@@ -66,6 +66,10 @@ void ysolve_factor(const YsolveDev& d, int ngroups, int ninst, double rank_tol, 
                    double* zsave = nullptr, const double* zuse = nullptr);
 // dynamic shared memory limits of the chain solves for groups up to max_group rows
 void ysolve_configure(int max_group);
+// the star elimination of the A_mom rows before (rho) and after (their y)
+// the solve on the other rows; shared by the dense and the sparse factor
+void ysolve_star_pre(const YsolveDev& d, const double* r, double* rho, cudaStream_t st);
+void ysolve_star_post(const YsolveDev& d, const double* r, double* y, cudaStream_t st);
 void ysolve_apply(const YsolveDev& d, int ninst, int max_group, const double* r, double* y, double* rho,
                   cudaStream_t st);
 

@@ -90,14 +90,14 @@ void enqueue_iteration(strom_solver* s, cudaStream_t st) {
   admm_block_mode(d, st);
   // Step 1: r = b/sigma - A(X/sigma + S - C), y^{k+1/2} = (A A^*)^{-1} r
   admm_residual_rhs(d, s->S.p, s->r.p, st);
-  ysolve_apply(yd, s->ninst, s->max_group, s->r.p, s->yh.p, s->rho.p, st);
+  ysolve_run(s, yd, s->r.p, s->yh.p, s->rho.p, st);
   // Step 2: X_b = X + sigma (A^* y - C), S = (Pi(X_b) - X_b) / sigma
   admm_xb(d, s->yh.p, s->Xb.p, st);
   psd_launch(psd_args(s, s->Xb.p, s->S.p, s->blk_act32.p, true, true), s->cls, STROM_PREC_FP32, st);
   psd_launch(psd_args(s, s->Xb.p, s->S.p, s->blk_act64.p, true, false, true), s->cls, STROM_PREC_FP64, st);
   // Step 3: r = b/sigma - A(X/sigma + S - C), y^{k+1} = (A A^*)^{-1} r
   admm_residual_rhs(d, s->S.p, s->r.p, st);
-  ysolve_apply(yd, s->ninst, s->max_group, s->r.p, s->y.p, s->rho.p, st);
+  ysolve_run(s, yd, s->r.p, s->y.p, s->rho.p, st);
   // Step 4: X = X + tau sigma (S + A^* y - C), residuals, stop test, sigma rule
   admm_xupdate(d, s->y.p, s->opt.tau, st);
   admm_primal_res(d, s->y.p, st);
@@ -338,16 +338,24 @@ void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
   s->inst_svec_chunk.upload(sfirst.data(), sfirst.size(), st);
   s->inst_row_chunk.upload(rfirst.data(), rfirst.size(), st);
   s->norm_C.upload(normC.data(), normC.size(), st);
-  s->fac.alloc(std::max<int64_t>(1, fac_acc));
-  s->lt.alloc(std::max<int64_t>(1, fac_acc));
-  s->coup.alloc(std::max<int64_t>(1, coup_acc));
-  s->diag0.alloc(std::max<size_t>(1, oth_rows.size()));
+  // the factorisation of the y-solve: dense per-clique groups or the sparse factor
+  {
+    int fk = s->opt.factor;
+    const double dense_bytes = 8.0 * (2.0 * (double)fac_acc + (double)coup_acc + (double)dinv_acc);
+    if (fk == STROM_FACTOR_AUTO) fk = (s->max_group <= 800 && dense_bytes <= 8e9) ? STROM_FACTOR_DENSE : STROM_FACTOR_SPARSE;
+    s->factor_kind = fk;
+  }
+  const bool dense = s->factor_kind == STROM_FACTOR_DENSE;
+  s->fac.alloc(dense ? std::max<int64_t>(1, fac_acc) : 1);
+  s->lt.alloc(dense ? std::max<int64_t>(1, fac_acc) : 1);
+  s->coup.alloc(dense ? std::max<int64_t>(1, coup_acc) : 1);
+  s->diag0.alloc(dense ? std::max<size_t>(1, oth_rows.size()) : 1);
   s->keep.alloc(s->m);
-  s->keep_oth.alloc(std::max<size_t>(1, oth_rows.size()));
-  s->yo.alloc(std::max<size_t>(1, oth_rows.size()));
+  s->keep_oth.alloc(dense ? std::max<size_t>(1, oth_rows.size()) : 1);
+  s->yo.alloc(dense ? std::max<size_t>(1, oth_rows.size()) : 1);
   s->yo.zero(st);
-  s->inv_piv.alloc(std::max<size_t>(1, oth_rows.size()));
-  s->dinv.alloc(std::max<int64_t>(1, dinv_acc));
+  s->inv_piv.alloc(dense ? std::max<size_t>(1, oth_rows.size()) : 1);
+  s->dinv.alloc(dense ? std::max<int64_t>(1, dinv_acc) : 1);
   s->dinv_off.upload(dinv_off.data(), dinv_off.size(), st);
   STROM_CUDA(cudaMemsetAsync(s->keep.p, 1, s->m, st));
   for (auto* v : {&s->X, &s->S, &s->Xb, &s->rho, &s->tmp_svec}) v->alloc(s->nsvec);
@@ -396,7 +404,8 @@ void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
       if (v == 1 || v == 2 || v == 4 || v == 8) yd.tile_r = v;
     }
   }
-  ysolve_configure(s->max_group);
+  if (dense) ysolve_configure(s->max_group);
+  else sparse_setup(s, sdps, count);
   AdmmDev& ad = s->ad;
   ad.ninst = count; ad.nblk = s->nblk;
   ad.n_svec_chunks = (int)sch.size(); ad.n_row_chunks = (int)rch.size();
@@ -442,6 +451,7 @@ extern "C" void strom_options_default(strom_options* o) {
   o->time_budget_s = 0.0;
   o->eig_warm_period = 20;
   o->share_tail = 1;
+  o->factor = STROM_FACTOR_AUTO;
 }
 
 extern "C" int strom_solver_create(const strom_sdp* const* sdps, int32_t count, const strom_options* opt,
@@ -455,7 +465,8 @@ extern "C" int strom_solver_create(const strom_sdp* const* sdps, int32_t count, 
     else strom_options_default(&s->opt);
     const auto& o = s->opt;
     if (!(o.tol > 0) || o.maxiter < 1 || !(o.sigma0 > 0) || !(o.tau > 0 && o.tau < 2) || !(o.rank_tol > 0) ||
-        o.precision < 0 || o.precision > 2 || o.check_every < 1 || o.eig_warm_period < 0)
+        o.precision < 0 || o.precision > 2 || o.check_every < 1 || o.eig_warm_period < 0 || o.factor < 0 ||
+        o.factor > 2)
       throw StatusError(STROM_ERR_INVALID, "strom_solver_create: invalid options");
     // the PSD kernels keep a block of up to 160 rows in shared memory
     for (int i = 0; i < count; ++i)
@@ -550,6 +561,10 @@ static void upload_groups(strom_solver* s, const std::vector<int>& inst, const s
 // the first group (all consensus rows), in pass 2 through instance 0's E.
 void strom::factor_instances(strom_solver* s, const std::vector<int>& inst, bool tail) {
   if (inst.empty()) return;
+  if (s->factor_kind == STROM_FACTOR_SPARSE) {
+    sparse_factor_instances(s, inst, tail);
+    return;
+  }
   cudaStream_t st = s->stream;
   const bool sh = s->shared_tail;
   if (sh && tail && inst.size() > 1 && std::find(inst.begin(), inst.end(), 0) != inst.end()) {
@@ -917,7 +932,7 @@ extern "C" int strom_kernel_solve(const strom_solver* s, const double* r_dev, do
     if (!s || !r_dev || !y_dev || r_dev == y_dev) throw StatusError(STROM_ERR_INVALID, "strom_kernel_solve: bad arguments");
     YsolveDev yd = s->yd;
     yd.inst_active = nullptr;
-    ysolve_apply(yd, s->ninst, s->max_group, r_dev, y_dev, const_cast<double*>(s->rho.p), (cudaStream_t)stream);
+    ysolve_run(const_cast<strom_solver*>(s), yd, r_dev, y_dev, const_cast<double*>(s->rho.p), (cudaStream_t)stream);
     return STROM_OK;
   });
 }
@@ -942,11 +957,13 @@ extern "C" int strom_solver_tune(strom_solver* s, int32_t reps, void* stream, st
     std::memset(out, 0, sizeof(*out));
     if (stream) STROM_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     cudaStream_t st = s->stream;
-    // candidate tiles: the multi-right-hand-side kernel needs the shared tail
+    // candidate tiles: several instances per CTA need the shared tail
+    const bool sparse = s->factor_kind == STROM_FACTOR_SPARSE;
     std::vector<int> cand = {1};
     if (s->shared_tail)
       for (int r : {2, 4, 8})
-        if (r <= s->ninst) cand.push_back(r);
+        if (r <= s->ninst && (!sparse || sizeof(double) * 2 * (size_t)r * s->sp.dev.max_group <= 200 * 1024))
+          cand.push_back(r);
     DevBuf<double> rhs, sol;
     rhs.alloc(s->m);
     sol.alloc(s->m);
@@ -956,13 +973,22 @@ extern "C" int strom_solver_tune(strom_solver* s, int32_t reps, void* stream, st
     yd.inst_active = nullptr;
     EventPair ev;
     ev.create();
-    int best = s->yd.tile_r;
+    const int old_tile = sparse ? s->sp.dev.tile_r : s->yd.tile_r;
+    int best = old_tile;
     double best_ms = -1.0;
+    auto set_tile = [&](int r) {
+      if (sparse) {
+        s->sp.dev.tile_r = r;
+        sparse_configure(s->sp.dev);
+      } else {
+        yd.tile_r = r;
+      }
+    };
     for (size_t c = 0; c < cand.size(); ++c) {
-      yd.tile_r = cand[c];
-      ysolve_apply(yd, s->ninst, s->max_group, rhs.p, sol.p, s->rho.p, st);  // warm-up
+      set_tile(cand[c]);
+      ysolve_run(s, yd, rhs.p, sol.p, s->rho.p, st);  // warm-up
       STROM_CUDA(cudaEventRecord(ev.a, st));
-      for (int k = 0; k < reps; ++k) ysolve_apply(yd, s->ninst, s->max_group, rhs.p, sol.p, s->rho.p, st);
+      for (int k = 0; k < reps; ++k) ysolve_run(s, yd, rhs.p, sol.p, s->rho.p, st);
       STROM_CUDA(cudaEventRecord(ev.b, st));
       STROM_CUDA(cudaEventSynchronize(ev.b));
       float ms = 0.0f;
@@ -974,10 +1000,11 @@ extern "C" int strom_solver_tune(strom_solver* s, int32_t reps, void* stream, st
         best = cand[c];
       }
     }
+    set_tile(best);
+    if (!sparse) s->yd.tile_r = best;
     out->ncand = (int32_t)cand.size();
     out->chosen = best;
-    if (best != s->yd.tile_r) {
-      s->yd.tile_r = best;
+    if (best != old_tile) {
       // the captured iteration holds the old launch shape: capture again on the next step
       if (s->graph) { STROM_CUDA(cudaGraphExecDestroy(s->graph)); s->graph = nullptr; }
       if (s->graph_def) { STROM_CUDA(cudaGraphDestroy(s->graph_def)); s->graph_def = nullptr; }

@@ -4,11 +4,40 @@
 
 #include <vector>
 
+#include <memory>
+
 #include "admm.cuh"
 #include "common.cuh"
 #include "factor.cuh"
+#include "sparse.cuh"
+#include "sparse.h"
 
 namespace strom {
+// one symbolic pattern of the sparse factor with its device copies; the
+// arrays only the factorisation reads (fac_*) may be dropped between
+// factorisations when several patterns would not fit together
+struct SpPatHost {
+  std::unique_ptr<SpSymbolic> sym;
+  DevBuf<int64_t> fptr, bptr, fsplit, bsplit;
+  DevBuf<int32_t> fcol, brow, grp_ptr, blk_grp, can_local;
+  DevBuf<int64_t> s_dst;
+  DevBuf<int32_t> fmap, s_ri, s_rj;
+  bool fac_on_device = false;
+};
+struct SparseState {
+  std::vector<std::unique_ptr<SpPatHost>> pats;
+  std::vector<int32_t> inst_pat;       // pattern of each instance
+  std::vector<SpInstDev> inst_h;
+  std::vector<SpPatDev> pats_h;
+  DevBuf<SpPatDev> pats_dev;
+  DevBuf<SpInstDev> inst_dev;
+  DevBuf<double> fval, bval, dinv, dinvb, sdiag, w;
+  bool keep_fac = true;                // factorisation arrays stay on the device
+  int max_n = 0;
+  SpDev dev{};
+  int64_t fval_entries = 0;            // values stored (all instances)
+  double symbolic_s = 0.0;             // host time of the symbolic analysis
+};
 struct InstMeta {
   int N, nv, dx, du;
   int64_t nsvec, m;
@@ -64,6 +93,8 @@ struct strom_solver {
   YsolveDev yd{};
   AdmmDev ad{};
   AdmmParams prm{};
+  int factor_kind = STROM_FACTOR_DENSE;  // the factorisation in use (DENSE or SPARSE)
+  strom::SparseState sp;
   cudaStream_t stream = nullptr;
   cudaGraphExec_t graph = nullptr;
   cudaGraph_t graph_def = nullptr;
@@ -83,4 +114,9 @@ void factor_instances(strom_solver* s, const std::vector<int>& inst, bool tail =
 void eig_instances(strom_solver* s, const std::vector<int>& inst, bool use_Z, std::vector<double>& lam,
                    std::vector<double>& topvec, std::vector<int64_t>& lam_off);
 int run_iterations(strom_solver* s, int iters, cudaStream_t user, int32_t* n_active);
+// sparse factor (sparse_solver.cu)
+void sparse_setup(strom_solver* s, const strom_sdp* const* sdps, int count);
+void sparse_factor_instances(strom_solver* s, const std::vector<int>& inst, bool tail);
+// y = (A_K A_K^T)^{-1} r with the factor in use; yd.inst_active selects instances
+void ysolve_run(strom_solver* s, const YsolveDev& yd, const double* r, double* y, double* rho, cudaStream_t st);
 }  // namespace strom

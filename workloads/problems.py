@@ -125,8 +125,8 @@ def pendulum_problem(N: int = 10, dt: float = 0.1, theta0: float = 0.1, g_l: flo
         e3 = W1 - W0 - (dt / w_max) * (u_max * U - g_l * S0)
         e4 = C1 * C1 + S1 * S1 - 1.0
         h = [e1, e2, e3, e4]
-        if k == 1:
-            h += [C0 - np.cos(theta0), S0 - np.sin(theta0), W0 - omega0 / w_max]
+        if k == 1:  # the initial state first: the same constraints, less fill in the y-solve's factor
+            h = [C0 - np.cos(theta0), S0 - np.sin(theta0), W0 - omega0 / w_max] + h
         g = [1.0 - U * U, 1.0 - W1 * W1]
         raw.append((f, g, h))
     fscale = 1.0 / max(f.max_abs_coef() for f, _, _ in raw)
@@ -223,8 +223,8 @@ def cartpole_problem(N: int = 50, dt: float = 0.05, x0: float = 0.0, theta0: flo
         e1, e2 = _cayley(C0, S0, W0, C1, S1, hw)
         e_c = C1 * C1 + S1 * S1 - 1.0
         h = [e_x, e_v, e_w, e1, e2, e_c]
-        if k == 1:
-            h += [X0 - x0 / x_max, V0 - 0.0, C0 - np.cos(theta0), S0 - np.sin(theta0), W0 - 0.0]
+        if k == 1:  # the initial state first: the same constraints, less fill in the y-solve's factor
+            h = [X0 - x0 / x_max, V0 - 0.0, C0 - np.cos(theta0), S0 - np.sin(theta0), W0 - 0.0] + h
         gg = [1.0 - F * F, 1.0 - X1 * X1, 1.0 - V1 * V1, 1.0 - W1 * W1]
         raw.append((stage, gg, h))
     fscale = 1.0 / max(f.max_abs_coef() for f, _, _ in raw)
@@ -265,10 +265,10 @@ def rigid_body_problem(N: int = 20, dt: float = 0.1, start=(-0.8, -0.8, 0.0), go
         e1, e2 = _cayley(C0, S0, W0, C1, S1, hw)
         e_c = C1 * C1 + S1 * S1 - 1.0
         h = [e_rx, e_ry, e_vx, e_vy, e_w, e1, e2, e_c]
-        if k == 1:
+        if k == 1:  # the initial state first: the same constraints, less fill in the y-solve's factor
             sx, sy, sth = start
-            h += [RX0 - sx / p_max, RY0 - sy / p_max, C0 - np.cos(sth), S0 - np.sin(sth),
-                  VX0 - 0.0, VY0 - 0.0, W0 - 0.0]
+            h = [RX0 - sx / p_max, RY0 - sy / p_max, C0 - np.cos(sth), S0 - np.sin(sth),
+                 VX0 - 0.0, VY0 - 0.0, W0 - 0.0] + h
         gg = [1.0 - FC * FC - FS * FS, 1.0 - VX1 * VX1, 1.0 - VY1 * VY1, 1.0 - W1 * W1]
         for (ox, oy, rho) in disks:
             gg.append((RX1 - ox / p_max) ** 2 + (RY1 - oy / p_max) ** 2 - (rho / p_max) ** 2)
