@@ -8,13 +8,14 @@ max(eta_p, eta_d, eta_g) <= 1e-8 (the objective parity of a GPU solve at
 that solution. Only oracle/ computes; workloads/ supplies the seeded inputs.
 
 Sets (instance i of a set is workloads.problem_batch(kind, ...)[i]):
-  pendulum    N = 10, seeds 0..7 of the pendulum batch
+  pendulum    N = 10, seeds 0..15 of the pendulum batch (0..7: batched solves;
+              all 16: requests of a served batch)
   cartpole    N = 50, seeds 0..7 of the cart-pole batch
   rigid_body  the 8 instances of the 128-instance uneven batch
               (N ~ U{20..100}) with the shortest horizons
 
 Usage: python tests/golden/make_oracle_refs.py SET [SET ...] [--workers K]
-Existing entries of other sets are kept. Single-threaded BLAS per worker.
+Existing entries are kept; only missing ones are computed. Single-threaded BLAS per worker.
 """
 from __future__ import annotations
 
@@ -36,7 +37,7 @@ def instances(kind):
     sys.path.insert(0, ROOT)
     import workloads as wl
     if kind == "pendulum":
-        ps = wl.problem_batch("pendulum", 8, N=10)
+        ps = wl.problem_batch("pendulum", 16, N=10)
         return [(i, p) for i, p in enumerate(ps)]
     if kind == "cartpole":
         ps = wl.problem_batch("cartpole", 8, N=50)
@@ -75,8 +76,8 @@ def main(argv):
         argv = argv[:k] + argv[k + 2:]
     os.environ["OMP_NUM_THREADS"] = "1"
     os.environ["OPENBLAS_NUM_THREADS"] = "1"
-    jobs = [(kind, i) for kind in argv for i, _ in instances(kind)]
     refs = json.load(open(OUT)) if os.path.exists(OUT) else {}
+    jobs = [(kind, i) for kind in argv for i, _ in instances(kind) if str(i) not in refs.get(kind, {})]
     import multiprocessing as mp
     with mp.get_context("spawn").Pool(workers) as pool:
         for r in pool.imap_unordered(solve_one, jobs):

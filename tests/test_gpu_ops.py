@@ -6,7 +6,7 @@ import workloads as wl
 from oracle import relax as OR
 from oracle import sgs_admm as OA
 
-from gpu_common import dev, host, lib, torch
+from gpu_common import assert_close, dev, host, lib, torch
 
 pytestmark = pytest.mark.gpu
 
@@ -72,8 +72,7 @@ def test_ysolve_matches_oracle(pend_batch):
         want = OA.YSolver(red.A)(r[ro:ro + o.m][red.keep])
         got = y[ro:ro + o.m]
         assert np.all(got[~red.keep] == 0.0)
-        err = np.linalg.norm(got[red.keep] - want) / np.linalg.norm(want)
-        assert err <= 1e-10, err
+        assert_close(got[red.keep], want, 1e-10, what=("y", i))
 
 
 _CART = {}
@@ -102,13 +101,13 @@ def test_cartpole_ysolve_and_iterations_match_oracle():
     solver.kernel_solve(rd.data_ptr(), yd.data_ptr())
     y = host(yd)
     want = OA.YSolver(red.A)(r[red.keep])
-    assert np.linalg.norm(y[red.keep] - want) <= 1e-10 * np.linalg.norm(want)
+    assert_close(y[red.keep], want, 1e-10, what="y")
     # the first 25 iterations of Algorithm 1
     solver.step(25)
     X, Sg, _ = solver.state(0)
     ref = OA.solve(red, OA.Options(tol=1e-12, maxiter=25))
-    assert np.linalg.norm(X - ref.X) <= 1e-9 * np.linalg.norm(ref.X)
-    assert np.linalg.norm(Sg - ref.S) <= 1e-9 * max(1.0, np.linalg.norm(ref.S))
+    assert_close(X, ref.X, 1e-9, what="X")
+    assert_close(Sg, ref.S, 1e-9, floor=1.0, what="S")
 
 
 @pytest.mark.parametrize("tile", ["2", "4", "8"])
@@ -135,4 +134,4 @@ def test_multi_rhs_solve_matches_single(tile, monkeypatch):
         red = OA.reduce(OR.relax(probs[i]))
         so, ro = one.offsets(i)
         want = OA.YSolver(red.A)(r[ro:ro + red.sdp.m][red.keep])
-        assert np.linalg.norm(b[ro:ro + red.sdp.m][red.keep] - want) <= 1e-10 * np.linalg.norm(want)
+        assert_close(b[ro:ro + red.sdp.m][red.keep], want, 1e-10, what=("y", i))

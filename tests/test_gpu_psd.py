@@ -21,13 +21,19 @@ def _project(S, x, off, n, prec):
 
 
 def _rel_errors(x, off, n, got):
+    """Per block, the larger of two relative errors of the projection: the
+    Frobenius norm ||G - Pi||_F / ||X||_F and the element-wise
+    max |G_ij - Pi_ij| / max |X_ij| (a wrong small entry of a large block
+    shows in the second)."""
     errs = []
     for o, k in zip(off, n):
         t = k * (k + 1) // 2
         X = OR.smat(x[o:o + t], k)
         want = OA.project_block(X)
         G = OR.smat(got[o:o + t], k)
-        errs.append(np.linalg.norm(G - want) / max(1e-300, np.linalg.norm(X)))
+        fro = np.linalg.norm(G - want) / max(1e-300, np.linalg.norm(X))
+        elem = np.max(np.abs(G - want)) / max(1e-300, np.max(np.abs(X)))
+        errs.append(max(fro, elem))
     return np.array(errs)
 
 

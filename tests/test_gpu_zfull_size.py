@@ -11,7 +11,7 @@ import workloads as wl
 from oracle import relax as OR
 from oracle import sgs_admm as OA
 
-from gpu_common import dev, host, lib, torch
+from gpu_common import assert_close, dev, host, lib, torch
 
 pytestmark = pytest.mark.gpu
 
@@ -40,7 +40,7 @@ def test_full_batch_ysolve_and_first_iteration_sampled():
         got = y[ro:ro + rr.sdp.m]
         want = OA.YSolver(rr.A)(r[ro:ro + rr.sdp.m][rr.keep])
         assert np.all(got[~rr.keep] == 0.0)
-        assert np.linalg.norm(got[rr.keep] - want) <= 1e-10 * np.linalg.norm(want)
+        assert_close(got[rr.keep], want, 1e-10, what=("y", i))
     # the first iteration of Algorithm 1: FP64, and mixed precision (FP32 eigensolver)
     fp64.step(1)
     mixed = S.Solver(sd, tol=1e-12, maxiter=1, precision=S.STROM_PREC_MIXED, check_every=1)
@@ -49,5 +49,5 @@ def test_full_batch_ysolve_and_first_iteration_sampled():
         ref = OA.solve(red[i], OA.Options(tol=1e-12, maxiter=1))
         for sv, tol in ((fp64, 1e-9), (mixed, 1e-5)):
             X, Sg, _ = sv.state(i)
-            assert np.linalg.norm(X - ref.X) <= tol * np.linalg.norm(ref.X)
-            assert np.linalg.norm(Sg - ref.S) <= tol * max(1.0, np.linalg.norm(ref.S))
+            assert_close(X, ref.X, tol, what=("X", i, tol))
+            assert_close(Sg, ref.S, tol, floor=1.0, what=("S", i, tol))

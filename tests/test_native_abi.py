@@ -161,7 +161,8 @@ def test_binding_constants_match_the_header():
     vals = {k: int(v) for k, v in re.findall(r"\b(STROM_[A-Z0-9_]+)\s*=\s*(-?\d+)", text)}
     vals.update({k: int(v) for k, v in re.findall(r"#define\s+(STROM_[A-Z0-9_]+)\s+(\d+)", text)})
     for k in ("STROM_OK", "STROM_MAXITER", "STROM_PENDING", "STROM_PREC_FP64", "STROM_PREC_FP32",
-              "STROM_PREC_MIXED", "STROM_WARM_MAX_KEY"):
+              "STROM_PREC_MIXED", "STROM_WARM_MAX_KEY", "STROM_ERR_INVALID", "STROM_ERR_OOM", "STROM_ERR_NOT_PD",
+              "STROM_ERR_NUMERICAL", "STROM_ERR_TIMEOUT", "STROM_ERR_CUDA"):
         assert getattr(N, k) == vals[k], k
     assert (OR.KIND_MOM, OR.KIND_INEQ, OR.KIND_EQ, OR.KIND_PHI0, OR.KIND_CONS) == \
         (vals["STROM_ROW_MOM"], vals["STROM_ROW_INEQ"], vals["STROM_ROW_EQ"], vals["STROM_ROW_PHI0"],

@@ -7,12 +7,12 @@ It contains none of the relaxation, ADMM or projection arithmetic; both the
 oracle and the CUDA path read what it produces.
 """
 from .poly import Poly
-from .problems import (Problem, Clique, toy_problem, pendulum_problem, paper_pendulum_problem,
+from .problems import (BASE_SEED, Problem, Clique, toy_problem, pendulum_problem, paper_pendulum_problem,
                        paper_landing_problem, paper_flying_robot_problem, paper_car_backin_problem,
                        cartpole_problem, rigid_body_problem, problem_batch)
 from .psd_bench import psd_microbench, known_spectrum_blocks
 
-__all__ = ["Poly", "Problem", "Clique", "toy_problem", "pendulum_problem", "paper_pendulum_problem",
+__all__ = ["BASE_SEED", "Poly", "Problem", "Clique", "toy_problem", "pendulum_problem", "paper_pendulum_problem",
            "paper_landing_problem", "paper_flying_robot_problem", "paper_car_backin_problem",
            "cartpole_problem", "rigid_body_problem", "problem_batch",
            "psd_microbench", "known_spectrum_blocks"]
