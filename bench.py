@@ -50,7 +50,11 @@ def parse():
     ap.add_argument("--maxiter", type=int, default=6000)
     ap.add_argument("--plain", type=int, default=1, help="instances timed in the plain FP64 single-instance form")
     ap.add_argument("--cpu-budget", type=float, default=25.0)
-    ap.add_argument("--workload", default="served", choices=["served", "psd", "warm", "poisson"],
+    ap.add_argument("--batch", type=int, default=0, help="cartpole / rigid workloads: instances (0 = 256 / 128)")
+    ap.add_argument("--horizon-batch", type=int, default=0,
+                    help="cartpole / rigid workloads: horizon (0 = 50 / N ~ U{20..100})")
+    ap.add_argument("--check", type=int, default=100, help="cartpole / rigid workloads: iterations between checks")
+    ap.add_argument("--workload", default="served", choices=["served", "psd", "warm", "poisson", "cartpole", "rigid"],
                     help="served: certified solves/s (default); psd: the 4096-block PSD-projection microbench; "
                          "warm: nearest-neighbour warm starts from a database of solved pendulums; "
                          "poisson: open-loop Poisson arrivals served cold and with warm starts from solved requests")
@@ -408,11 +412,23 @@ def roofline(S, solver, sdps, stream):
     torch.cuda.synchronize()
     t_psd = e0.elapsed_time(e1) / 1e3 / reps
     f_psd = psd_flops(ns.tolist())
-    # ALU peaks from unit counts and the maximum SM clock: 152 SMs x 2 FP64
-    # (128 FP32) FMA per clock x 2 flops x 2.07 GHz; an FMA-loop probe on
-    # this part measured 1.208 and 75.49 TFLOP/s
-    fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12
-    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    # ALU peaks from unit counts and the maximum SM clock: SMs x 2 FP64
+    # (128 FP32) FMA per clock x 2 flops x clock; an FMA-loop probe on this
+    # part measured 1.208 and 75.49 TFLOP/s
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    fp64_peak = sms * 2 * 2 * clk / 1e12
+    fp32_peak = sms * 128 * 2 * clk / 1e12
+    # the method's own work for the same solves: the sparse Cholesky factor
+    # of the star-eliminated system (strom_sdp_factor_info), 2 flops per
+    # stored entry forward and again backward
+    fi_cache = {}
+    for sd in sdps:
+        k = (sd.m, sd.nsvec)
+        if k not in fi_cache:
+            fi = sd.factor_info()
+            fi_cache[k] = 4 * fi["nnz_L"] + 4 * fi["n_other"]
+    f_sparse = sum(fi_cache[(sd.m, sd.nsvec)] for sd in sdps)
     # DRAM bytes (read + write) of one y-solve launch over 1024 pendulum
     # (N = 10) instances, from an ncu capture of the unchanged kernel
     traffic = 1.708e9 + 39.6e6 if (len(sdps) == 1024 and sdps[0].info.N == 10) else None
@@ -422,7 +438,12 @@ def roofline(S, solver, sdps, stream):
                  if len(sdps) >= 304 else "chain_solve_kernel")
         return {"kernel": "chain y-solve, FP64: " + kname, "bound": "alu", "achieved": ach,
                 "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak, "traffic": traffic,
-                "peak_basis": "unit counts x 2.07 GHz (FMA-loop probe: 1.208 TFLOP/s FP64)",
+                "peak_basis": "%d SMs x 2 FP64 FMA/clk x %.2f GHz (FMA-loop probe: 1.208 TFLOP/s FP64)"
+                              % (sms, clk / 1e9),
+                "method_work": {"flops_per_launch": f_sparse, "achieved": f_sparse / t_solve / 1e12,
+                                "frac": f_sparse / t_solve / 1e12 / fp64_peak,
+                                "basis": "sparse Cholesky factor of the star-eliminated system (4 flops per "
+                                         "stored entry per solve): the work the method needs"},
                 "launch_ms": 1e3 * t_solve, "other": {"jacobi_psd_fp32_ms": 1e3 * t_psd,
                                                       "jacobi_psd_fp32_tflops": f_psd / t_psd / 1e12}}
     ach = f_psd / t_psd / 1e12
@@ -597,6 +618,117 @@ def run_psd(a):
             "roofline": {"kernel": "jacobi_psd_kernel", "bound": "alu", "achieved": flops / t / 1e12, "peak": fp,
                          "unit": "TFLOP/s", "frac": flops / t / 1e12 / fp, "traffic": None,
                          "algorithmic_flops": flops},
+            "clocks": clocks}
+    print(json.dumps(line))
+
+
+def _oracle_refs(kind):
+    """The FP64 oracle's stored reference solves (tests/golden/oracle_refs.json,
+    written by tests/golden/make_oracle_refs.py from oracle/ alone)."""
+    try:
+        return json.load(open(os.path.join(ROOT, "tests", "golden", "oracle_refs.json"))).get(kind, {})
+    except OSError:
+        return {}
+
+
+def run_batch(a):
+    """One batched solve of many instances in one solver (configs 3 and 4):
+    the cart-pole swing-up x256 at N = 50, or the planar rigid body x128 with
+    horizons N ~ U{20..100} and 2-4 disk obstacles. FP32 Jacobi eigensolver
+    with the FP64 polish, FP64 sparse factor of the y-solve. A step is the
+    whole solve: set-up from device-resident data (row reduction,
+    factorisation), Algorithm 1 until every instance met KKT <= 1e-6 or
+    maxiter, certificates. Reported: certified solves/s, the time at which
+    each instance was seen converged (p50/p99, checked every check_every
+    iterations), and the objectives of the instances that have an oracle
+    reference."""
+    import numpy as np
+    import torch
+    import paper_2406_05846_gb300 as S
+    import workloads as wl
+    S.lib()
+    kind = "cartpole" if a.workload == "cartpole" else "rigid_body"
+    B = a.batch or (256 if kind == "cartpole" else 128)
+    kw = {"N": a.horizon_batch or 50} if kind == "cartpole" else ({"N": a.horizon_batch} if a.horizon_batch else {})
+    probs = wl.problem_batch(kind, B, **kw)
+    t0 = time.perf_counter()
+    P, sdps = relax_all(S, probs)
+    t_relax = time.perf_counter() - t0
+    opts = dict(tol=1e-6, maxiter=a.maxiter, precision=S.STROM_PREC_MIXED, polish_eta=a.polish_eta,
+                check_every=a.check, factor=S.STROM_FACTOR_SPARSE)
+    t0 = time.perf_counter()
+    sv = S.Solver(sdps, **opts)
+    torch.cuda.synchronize()
+    t_create = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    for _ in range(a.warmup):     # graph capture, module loading, first-touch
+        sv.step(a.check, sp)
+    torch.cuda.synchronize()
+    clk = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clk.start()
+    l0 = S.launch_count()
+    e0, e1, ef = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    t0 = time.perf_counter()
+    e0.record(stream)
+    sv.factor(sp)
+    ef.record(stream)
+    seen = np.full(B, np.nan)
+    done_it = 0
+    while done_it < a.maxiter:
+        act = sv.step(a.check, sp)
+        done_it += a.check
+        now = time.perf_counter() - t0
+        for i in np.nonzero(np.isnan(seen))[0]:
+            if sv.result(int(i)).status != S.STROM_MAXITER or act == 0:
+                seen[i] = now
+        if act == 0:
+            break
+    certs = sv.certify_batch(P)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    t_setup = e0.elapsed_time(ef) / 1e3
+    clocks = clk.stop()
+    launches = S.launch_count() - l0
+    res = [sv.result(i) for i in range(B)]
+    conv = [r.status == S.STROM_OK for r in res]
+    ok = [c and cert.certified for c, cert in zip(conv, certs)]
+    iters = np.array([r.iterations for r in res])
+    lat = seen[np.array(conv)] if any(conv) else np.array([np.nan])
+    refs = _oracle_refs(kind)
+    parity = []
+    for i in range(B):
+        ref = refs.get(str(i)) if kind == "cartpole" else next(
+            (v for v in refs.values() if v["index"] == i), None)
+        if ref is None or not ref.get("converged") or not conv[i]:
+            continue
+        parity.append({"i": i, "rel_obj": abs(res[i].pobj - ref["pobj"]) / (1 + abs(ref["pobj"])),
+                       "verdict_equal": bool(certs[i].certified == ref["certified"])})
+    Ns = [p.N for p in probs]
+    line = {"metric": METRIC, "value": sum(ok) / t, "unit": "solves/s", "n_gpus": 1, "steps": 1,
+            "warmup": a.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": ("cart-pole swing-up x%d, N=%d, dt=0.05 (x0~U(-0.5,0.5), theta0~U(-0.3,0.3) "
+                                    "seeded)" % (B, Ns[0])) if kind == "cartpole" else
+                       ("planar rigid body x%d, N in [%d, %d] (mean %.1f), 2-4 disks seeded" %
+                        (B, min(Ns), max(Ns), float(np.mean(Ns)))),
+                       "instances": B, "maxiter": a.maxiter, "check_every": a.check,
+                       "precision": "FP32 Jacobi eig, FP64 polish once eta<=%g, FP64 sparse y-solve factor"
+                                    % a.polish_eta,
+                       "inputs": "resident in HBM; the step re-runs the set-up (row reduction, factorisation) "
+                                 "from device data"},
+            "completed": B, "converged": int(sum(conv)), "maxiter_hit": int(sum(r.status == S.STROM_MAXITER
+                                                                            for r in res)),
+            "certified": int(sum(ok)), "gpu_launches": launches,
+            "seconds": {"relax_host": t_relax, "solver_create": t_create, "setup_in_step": t_setup, "step": t},
+            "latency_s": {"converged_p50": float(np.percentile(lat, 50)),
+                          "converged_p99": float(np.percentile(lat, 99))},
+            "iterations": {"p50": float(np.percentile(iters, 50)), "p99": float(np.percentile(iters, 99)),
+                           "max": int(iters.max())},
+            "oracle_parity": {"instances": len(parity),
+                              "max_rel_obj": max((p["rel_obj"] for p in parity), default=None),
+                              "verdicts_equal": sum(p["verdict_equal"] for p in parity)},
             "clocks": clocks}
     print(json.dumps(line))
 
@@ -809,7 +941,10 @@ def run_poisson(a):
 def main():
     a = parse()
     rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", str(a.gpus if a.gpus == 1 else 1)))
+    if a.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit("bench.py --gpus %d: launch one process per GPU with torch.distributed.run "
+                 "(--nproc-per-node %d); a single process measures one GPU" % (a.gpus, a.gpus))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     if a.profile != "none":
         run_profile(a)
     elif a.impl == "reference":
@@ -820,6 +955,8 @@ def main():
         run_warm(a)
     elif a.workload == "poisson":
         run_poisson(a)
+    elif a.workload in ("cartpole", "rigid"):
+        run_batch(a)
     else:
         run_strom(a, rank, world)
 

@@ -369,6 +369,22 @@ int strom_moment_rank_test(const double* M, int32_t nv, const uint8_t* vars, dou
 typedef struct strom_batch strom_batch;
 
 int strom_batch_create(const strom_sdp* tmpl, int32_t slots, const strom_options* opt, strom_batch** out);
+/* Device bytes of a batch of this structure and options, measured on the
+ * current device by building solvers of one and two slots (their set-up
+ * included): *base_bytes once per batch, *slot_bytes per slot, and
+ * *transient_bytes of scratch that the set-up holds for a moment. Either of
+ * base_bytes / transient_bytes may be NULL. Admission by memory footprint
+ * (serving by an HBM budget) has no counterpart in the paper. */
+int strom_batch_slot_bytes(const strom_sdp* tmpl, const strom_options* opt, int64_t* base_bytes,
+                           int64_t* slot_bytes, int64_t* transient_bytes);
+/* A batch sized by a device-memory budget: as many slots as
+ * base + transient + slots x slot_bytes <= budget_bytes allows
+ * (strom_batch_slot_bytes); *slots_out (nullable) receives the count.
+ * Requests beyond the slots wait in the batch's queue (host memory).
+ * Errors: OOM when budget_bytes exceeds the device's free memory (nothing is
+ * allocated then), INVALID when the budget holds less than one slot. */
+int strom_batch_create_budget(const strom_sdp* tmpl, int64_t budget_bytes, const strom_options* opt,
+                              strom_batch** out, int32_t* slots_out);
 void strom_batch_destroy(strom_batch* b);
 /* Copies the request. problem (nullable): certify the result on completion.
  * X0, S0 (nullable, length nsvec): warm start of Algorithm 1.

@@ -8,6 +8,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libstrom.so")
 
 STROM_OK, STROM_MAXITER, STROM_PENDING = 0, 1, 2
+STROM_ERR_INVALID, STROM_ERR_OOM, STROM_ERR_NOT_PD, STROM_ERR_NUMERICAL, STROM_ERR_TIMEOUT, STROM_ERR_CUDA = (
+    -1, -2, -3, -4, -5, -6)
 STROM_PREC_FP64, STROM_PREC_FP32, STROM_PREC_MIXED = 0, 1, 2
 STROM_FACTOR_AUTO, STROM_FACTOR_DENSE, STROM_FACTOR_SPARSE = 0, 1, 2
 STROM_WARM_MAX_KEY = 8
@@ -124,6 +126,8 @@ SIGNATURES = {
     "strom_kernel_solve": (C.c_int, [P, P, P, P]),
     "strom_solver_tune": (C.c_int, [P, C.c_int32, P, C.POINTER(strom_tune_report)]),
     "strom_batch_create": (C.c_int, [P, C.c_int32, C.POINTER(strom_options), C.POINTER(P)]),
+    "strom_batch_slot_bytes": (C.c_int, [P, C.POINTER(strom_options), PI64, PI64, PI64]),
+    "strom_batch_create_budget": (C.c_int, [P, C.c_int64, C.POINTER(strom_options), C.POINTER(P), PI32]),
     "strom_batch_destroy": (None, [P]),
     "strom_batch_submit": (C.c_int, [P, P, P, PD, PD, C.POINTER(C.c_uint64)]),
     "strom_batch_step": (C.c_int, [P, C.c_int32, P, PI32, PI32]),

@@ -429,6 +429,36 @@ class Batch:
         self.handle = h
         self.slots = slots
 
+    @staticmethod
+    def slot_bytes(template: Sdp, **opts) -> int:
+        """strom_batch_slot_bytes: device bytes per slot of a batch of this structure."""
+        o = default_options(**opts)
+        b, p, t = C.c_int64(), C.c_int64(), C.c_int64()
+        check(lib().strom_batch_slot_bytes(template.handle, C.byref(o), C.byref(b), C.byref(p), C.byref(t)),
+              "strom_batch_slot_bytes")
+        return p.value
+
+    @staticmethod
+    def footprint(template: Sdp, **opts) -> dict:
+        """strom_batch_slot_bytes: {'base', 'slot', 'transient'} device bytes."""
+        o = default_options(**opts)
+        b, p, t = C.c_int64(), C.c_int64(), C.c_int64()
+        check(lib().strom_batch_slot_bytes(template.handle, C.byref(o), C.byref(b), C.byref(p), C.byref(t)),
+              "strom_batch_slot_bytes")
+        return {"base": b.value, "slot": p.value, "transient": t.value}
+
+    @classmethod
+    def with_budget(cls, template: Sdp, budget_bytes: int, **opts) -> "Batch":
+        """strom_batch_create_budget: as many slots as budget_bytes of device memory hold."""
+        self = cls.__new__(cls)
+        self.opt = default_options(**opts)
+        h, n = C.c_void_p(), C.c_int32()
+        check(lib().strom_batch_create_budget(template.handle, int(budget_bytes), C.byref(self.opt), C.byref(h),
+                                              C.byref(n)), "strom_batch_create_budget")
+        self.handle = h
+        self.slots = n.value
+        return self
+
     def __del__(self):
         if getattr(self, "handle", None):
             lib().strom_batch_destroy(self.handle)

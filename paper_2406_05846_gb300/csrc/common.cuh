@@ -1,6 +1,7 @@
 // Device/host helpers shared by the CUDA translation units of libstrom.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <stdexcept>
 #include <string>
@@ -24,6 +25,14 @@ struct StatusError : std::runtime_error {
   StatusError(int s, const std::string& m) : std::runtime_error(m), status(s) {}
 };
 
+// Device bytes allocated through DevBuf by the calling host thread while a
+// tally is attached (strom_batch_slot_bytes measures a solver's footprint
+// with it): live bytes and their peak.
+struct AllocTally {
+  int64_t live = 0, peak = 0;
+};
+inline thread_local AllocTally* g_alloc_tally = nullptr;
+
 template <typename T>
 struct DevBuf {
   T* p = nullptr;
@@ -33,7 +42,10 @@ struct DevBuf {
   DevBuf& operator=(const DevBuf&) = delete;
   ~DevBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) {
+      cudaFree(p);
+      if (g_alloc_tally) g_alloc_tally->live -= (int64_t)(n * sizeof(T));
+    }
     p = nullptr;
     n = 0;
   }
@@ -46,6 +58,10 @@ struct DevBuf {
       throw StatusError(STROM_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
     }
     n = count;
+    if (g_alloc_tally) {
+      g_alloc_tally->live += (int64_t)(count * sizeof(T));
+      if (g_alloc_tally->live > g_alloc_tally->peak) g_alloc_tally->peak = g_alloc_tally->live;
+    }
   }
   void upload(const T* h, size_t count, cudaStream_t st = 0) {
     alloc(count);
@@ -55,6 +71,16 @@ struct DevBuf {
   void zero(cudaStream_t st = 0) {
     if (n) STROM_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), st));
   }
+};
+
+// NVTX range over a host-side phase (set-up, factorisation, iterations,
+// certificate, admission, retirement), visible to a profiler's timeline;
+// without a profiler attached it costs a null check
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }

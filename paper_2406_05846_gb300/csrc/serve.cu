@@ -3,10 +3,13 @@
 // so a slow request never holds up the others.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
+#include <climits>
 #include <cmath>
 #include <deque>
 #include <memory>
+#include <string>
 #include <unordered_map>
 #include <vector>
 
@@ -81,6 +84,7 @@ int guard(F&& f) {
 }
 
 void admit(strom_batch* B) {
+  NvtxRange nv("strom.batch.admit");
   strom_solver* s = B->s;
   std::vector<int> adm;
   for (int i = 0; i < B->slots && !B->queue.empty(); ++i) {
@@ -131,6 +135,7 @@ void admit(strom_batch* B) {
 }
 
 void retire(strom_batch* B) {
+  NvtxRange nv("strom.batch.retire");
   strom_solver* s = B->s;
   const int n = s->ninst;
   std::vector<uint8_t> flag(n);
@@ -180,6 +185,75 @@ void retire(strom_batch* B) {
 }
 
 }  // namespace
+
+namespace {
+
+// Device footprint of a batch of this structure: a solver of one slot and one
+// of two slots are built (set-up included: row reduction and factorisation)
+// with the allocation tally attached. The second slot's bytes are the bytes
+// of every further slot (every slot but the first refers to the first one's
+// shared tail factor); the peak minus the resident bytes is the transient
+// scratch of the set-up.
+void slot_bytes(const strom_sdp* tmpl, const strom_options* opt, int64_t* base, int64_t* per_slot,
+                int64_t* transient) {
+  int64_t live[2], peak[2];
+  for (int k = 0; k < 2; ++k) {
+    AllocTally t;
+    AllocTally* prev = g_alloc_tally;
+    g_alloc_tally = &t;
+    strom_solver* s = nullptr;
+    const strom_sdp* v[2] = {tmpl, tmpl};
+    const int st = strom_solver_create(v, k + 1, opt, &s);
+    g_alloc_tally = prev;
+    live[k] = t.live;
+    peak[k] = t.peak;
+    strom_solver_destroy(s);
+    if (st != STROM_OK) throw StatusError(st, std::string("strom_batch_slot_bytes: ") + strom_last_error());
+  }
+  *per_slot = std::max<int64_t>(1, live[1] - live[0]);
+  *base = std::max<int64_t>(0, live[0] - *per_slot);
+  *transient = std::max<int64_t>(0, std::max(peak[0] - live[0], peak[1] - live[1]));
+}
+
+}  // namespace
+
+extern "C" int strom_batch_slot_bytes(const strom_sdp* tmpl, const strom_options* opt, int64_t* base_bytes,
+                                      int64_t* slot_bytes_out, int64_t* transient_bytes) {
+  return guard([&]() -> int {
+    if (!tmpl || !tmpl->s || !slot_bytes_out) throw StatusError(STROM_ERR_INVALID, "strom_batch_slot_bytes: bad arguments");
+    int64_t b = 0, p = 0, t = 0;
+    slot_bytes(tmpl, opt, &b, &p, &t);
+    if (base_bytes) *base_bytes = b;
+    *slot_bytes_out = p;
+    if (transient_bytes) *transient_bytes = t;
+    return STROM_OK;
+  });
+}
+
+extern "C" int strom_batch_create_budget(const strom_sdp* tmpl, int64_t budget_bytes, const strom_options* opt,
+                                         strom_batch** out, int32_t* slots_out) {
+  return guard([&]() -> int {
+    if (!tmpl || !tmpl->s || !out || budget_bytes <= 0)
+      throw StatusError(STROM_ERR_INVALID, "strom_batch_create_budget: bad arguments");
+    size_t free_b = 0, total_b = 0;
+    STROM_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    if ((uint64_t)budget_bytes > (uint64_t)free_b)
+      throw StatusError(STROM_ERR_OOM, "strom_batch_create_budget: budget of " + std::to_string(budget_bytes) +
+                                           " bytes exceeds the device's free memory (" + std::to_string(free_b) +
+                                           " bytes)");
+    int64_t base = 0, per = 0, tr = 0;
+    slot_bytes(tmpl, opt, &base, &per, &tr);
+    const int64_t room = budget_bytes - base - tr;
+    const int64_t slots = room > 0 ? room / per : 0;
+    if (slots < 1)
+      throw StatusError(STROM_ERR_INVALID, "strom_batch_create_budget: budget below one slot (" +
+                                               std::to_string(base + tr + per) + " bytes)");
+    if (slots > INT32_MAX) throw StatusError(STROM_ERR_INVALID, "strom_batch_create_budget: too many slots");
+    const int st = strom_batch_create(tmpl, (int32_t)slots, opt, out);
+    if (st == STROM_OK && slots_out) *slots_out = (int32_t)slots;
+    return st;
+  });
+}
 
 extern "C" int strom_batch_create(const strom_sdp* tmpl, int32_t slots, const strom_options* opt, strom_batch** out) {
   return guard([&]() -> int {

@@ -165,6 +165,7 @@ bool same_tail(const Sdp& a, const Sdp& b) {
 }
 
 void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
+  NvtxRange nv("strom.setup");
   s->ninst = count;
   s->svec_off.assign(count + 1, 0);
   s->row_off.assign(count + 1, 0);
@@ -497,6 +498,7 @@ extern "C" int strom_solver_offsets(const strom_solver* s, int32_t i, int64_t* s
 }
 
 int strom::run_iterations(strom_solver* s, int iters, cudaStream_t user, int32_t* n_active) {
+  NvtxRange nv("strom.iterations");
   build_graph(s);
   if (user) {  // order after the caller's prior work
     cudaEvent_t ev;
@@ -561,6 +563,7 @@ static void upload_groups(strom_solver* s, const std::vector<int>& inst, const s
 // the first group (all consensus rows), in pass 2 through instance 0's E.
 void strom::factor_instances(strom_solver* s, const std::vector<int>& inst, bool tail) {
   if (inst.empty()) return;
+  NvtxRange nv("strom.factor");
   if (s->factor_kind == STROM_FACTOR_SPARSE) {
     sparse_factor_instances(s, inst, tail);
     return;
@@ -1040,6 +1043,7 @@ __global__ void z_kernel(const int64_t* atptr, const int32_t* atrow, const doubl
 // instances, for X or Z = C - A^T y; lam_off receives the global offsets
 void strom::eig_instances(strom_solver* s, const std::vector<int>& inst, bool use_Z, std::vector<double>& lam,
                           std::vector<double>& topvec, std::vector<int64_t>& lam_off) {
+  NvtxRange nv("strom.certify.eig");
   const double* in = s->X.p;
   if (use_Z) {
     for (int i : inst) {
