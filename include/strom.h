@@ -400,6 +400,51 @@ int strom_batch_step(strom_batch* b, int32_t iters, void* stream, int32_t* n_run
 int strom_batch_poll(strom_batch* b, uint64_t ticket, strom_result* r, strom_certificate* c, double* latency_s,
                      double* service_s);
 /* ------------------------------------------------------------------------
+ * Serving several structures (robots, horizons) behind one front within one
+ * device-memory budget. The server routes each request to a class: the
+ * structure of the first request of its kind and, when opt->share_tail is
+ * set, that request's constraint values after the first clique; requests of
+ * a known structure whose later constraints differ (other obstacles) go to
+ * a second class of that structure without a shared tail factor. Each class
+ * gets a strom_batch on the first step after its first request, with
+ * min(max_slots, what the remaining budget holds) slots
+ * (strom_batch_slot_bytes). When no slot fits, idle batches of other
+ * classes are destroyed to make room (their results stay readable). A step
+ * runs every batch with work for `iters` iterations, each from its own host
+ * thread and stream, so different structures overlap on the device; each
+ * request's arithmetic is the same as solving it alone. Inputs are copied at
+ * submit. Latency counts the wait for a batch. The paper has no
+ * counterpart (its nearest use is the warm-started MPC loop of Sec. 5).
+ * Errors: strom_server_create returns OOM (allocating nothing) when
+ * budget_bytes exceeds the device's free memory.
+ * ---------------------------------------------------------------------- */
+typedef struct strom_server strom_server;
+typedef struct {
+  int32_t N;                 /* horizon of the class's structure */
+  int32_t shared_tail;       /* its batch shares the factor of cliques 2..N */
+  int64_t nsvec, m;
+  int32_t slots;             /* slots of its current batch (0: none) */
+  int32_t running, queued;   /* requests in the batch's slots / queue */
+  int32_t waiting;           /* requests waiting for a batch */
+  int32_t batches_created;
+  int32_t pad;
+  int64_t slot_bytes, reserved_bytes;
+} strom_server_class;
+int strom_server_create(int64_t budget_bytes, int32_t max_slots, const strom_options* opt, strom_server** out);
+void strom_server_destroy(strom_server* s);
+int strom_server_submit(strom_server* s, const strom_sdp* sdp, const strom_problem* problem, uint64_t* ticket);
+/* *n_running: requests in batches (slots and batch queues); *n_waiting:
+ * requests whose class has no batch yet. */
+int strom_server_step(strom_server* s, int32_t iters, void* stream, int32_t* n_running, int32_t* n_waiting);
+/* As strom_batch_poll. */
+int strom_server_poll(strom_server* s, uint64_t ticket, strom_result* r, strom_certificate* c, double* latency_s,
+                      double* service_s);
+/* The first min(cap, classes) classes into out; *nclass = classes;
+ * *used_bytes = budget bytes reserved by the current batches. */
+int strom_server_info(const strom_server* s, int32_t cap, strom_server_class* out, int32_t* nclass,
+                      int64_t* used_bytes);
+
+/* ------------------------------------------------------------------------
  * Data-driven warm starts (Sec. 5, inverted pendulum initialised by a
  * nearest-neighbour search over stored solutions). A store holds solved
  * states (X, S, sigma) of one SDP structure in device memory (capacity x 2 x

@@ -83,6 +83,13 @@ PI8 = C.POINTER(C.c_int8)
 PU8 = C.POINTER(C.c_uint8)
 
 # name: (restype, argtypes)
+class strom_server_class(C.Structure):
+    _fields_ = [("N", C.c_int32), ("shared_tail", C.c_int32), ("nsvec", C.c_int64), ("m", C.c_int64),
+                ("slots", C.c_int32), ("running", C.c_int32), ("queued", C.c_int32), ("waiting", C.c_int32),
+                ("batches_created", C.c_int32), ("pad", C.c_int32), ("slot_bytes", C.c_int64),
+                ("reserved_bytes", C.c_int64)]
+
+
 class strom_tune_report(C.Structure):
     _fields_ = [("ncand", C.c_int32), ("tile", C.c_int32 * 4), ("ms", C.c_double * 4), ("chosen", C.c_int32)]
 
@@ -127,6 +134,13 @@ SIGNATURES = {
     "strom_solver_tune": (C.c_int, [P, C.c_int32, P, C.POINTER(strom_tune_report)]),
     "strom_batch_create": (C.c_int, [P, C.c_int32, C.POINTER(strom_options), C.POINTER(P)]),
     "strom_batch_slot_bytes": (C.c_int, [P, C.POINTER(strom_options), PI64, PI64, PI64]),
+    "strom_server_create": (C.c_int, [C.c_int64, C.c_int32, C.POINTER(strom_options), C.POINTER(P)]),
+    "strom_server_destroy": (None, [P]),
+    "strom_server_submit": (C.c_int, [P, P, P, C.POINTER(C.c_uint64)]),
+    "strom_server_step": (C.c_int, [P, C.c_int32, P, PI32, PI32]),
+    "strom_server_poll": (C.c_int, [P, C.c_uint64, C.POINTER(strom_result), C.POINTER(strom_certificate),
+                                    C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "strom_server_info": (C.c_int, [P, C.c_int32, C.POINTER(strom_server_class), PI32, PI64]),
     "strom_batch_create_budget": (C.c_int, [P, C.c_int64, C.POINTER(strom_options), C.POINTER(P), PI32]),
     "strom_batch_destroy": (None, [P]),
     "strom_batch_submit": (C.c_int, [P, P, P, PD, PD, C.POINTER(C.c_uint64)]),

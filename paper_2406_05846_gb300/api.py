@@ -510,6 +510,60 @@ class Batch:
         return res, cert, lat.value
 
 
+class Server:
+    """strom_server: requests of several structures behind one front, one
+    batch per structure class, sized from one device-memory budget."""
+
+    def __init__(self, budget_bytes: int, max_slots: int, **opts):
+        self.opt = default_options(**opts)
+        h = C.c_void_p()
+        check(lib().strom_server_create(int(budget_bytes), int(max_slots), C.byref(self.opt), C.byref(h)),
+              "strom_server_create")
+        self.handle = h
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib().strom_server_destroy(self.handle)
+            self.handle = None
+
+    def submit(self, sdp: Sdp, problem: Problem | None = None) -> int:
+        t = C.c_uint64()
+        check(lib().strom_server_submit(self.handle, sdp.handle, problem.handle if problem else None, C.byref(t)),
+              "strom_server_submit")
+        return t.value
+
+    def step(self, iters: int, stream=None):
+        """Returns (requests in batches, requests waiting for a batch)."""
+        run, w = C.c_int32(), C.c_int32()
+        check(lib().strom_server_step(self.handle, iters, stream, C.byref(run), C.byref(w)), "strom_server_step")
+        return run.value, w.value
+
+    def poll(self, ticket: int, with_service=False):
+        """None while pending, else (Result, Certificate or None, latency_s[, service_s])."""
+        r, c, lat, svc = N.strom_result(), N.strom_certificate(), C.c_double(), C.c_double()
+        c.max_ratio = float("nan")
+        st = check(lib().strom_server_poll(self.handle, ticket, C.byref(r), C.byref(c), C.byref(lat), C.byref(svc)),
+                   "strom_server_poll")
+        if st == N.STROM_PENDING:
+            return None
+        res = Result(r.status, r.iterations, r.pobj, r.dobj, r.eta_p, r.eta_d, r.eta_g, r.sigma, r.m_kept)
+        cert = None
+        if c.max_ratio == c.max_ratio:
+            cert = Certificate(c.max_ratio, c.lower_bound, c.phat, c.xi, c.hmax, c.gmin, bool(c.feasible),
+                               bool(c.rank_one), bool(c.certified), None, None)
+        if with_service:
+            return res, cert, lat.value, svc.value
+        return res, cert, lat.value
+
+    def info(self):
+        """([per-class dict], bytes of the budget reserved by current batches)."""
+        n, used = C.c_int32(), C.c_int64()
+        check(lib().strom_server_info(self.handle, 0, None, C.byref(n), C.byref(used)), "strom_server_info")
+        arr = (N.strom_server_class * max(1, n.value))()
+        check(lib().strom_server_info(self.handle, n.value, arr, C.byref(n), C.byref(used)), "strom_server_info")
+        return [{k: getattr(arr[i], k) for k, _ in arr[i]._fields_ if k != "pad"} for i in range(n.value)], used.value
+
+
 class PsdPlan:
     """strom_psd_plan: PSD projection of a fixed list of svec blocks."""
 

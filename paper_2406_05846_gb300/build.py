@@ -13,7 +13,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libstrom.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU = ["psd.cu", "factor.cu", "admm.cu", "solver.cu", "serve.cu", "noalloc.cu", "warm.cu", "sparse.cu",
-      "sparse_solver.cu"]
+      "sparse_solver.cu", "server.cu"]
 CPP = ["relax.cpp", "capi.cpp", "certify.cpp", "warm_select.cpp", "sdp_import.cpp", "rank_test.cpp", "sparse_sym.cpp"]
 
 

@@ -12,11 +12,16 @@ namespace {
 thread_local std::string g_err;
 std::atomic<uint64_t> g_launches{0};
 std::atomic<uint64_t> g_h2d{0}, g_d2h{0};
+thread_local int64_t t_launches = 0;  // launches issued by this host thread
 }  // namespace
 
 namespace strom {
 void set_error(const std::string& msg) { g_err = msg; }
-void count_launches(int64_t n) { g_launches.fetch_add((uint64_t)n); }
+void count_launches(int64_t n) {
+  g_launches.fetch_add((uint64_t)n);
+  t_launches += n;
+}
+int64_t thread_launch_count() { return t_launches; }
 void count_h2d(uint64_t b) { g_h2d.fetch_add(b); }
 void count_d2h(uint64_t b) { g_d2h.fetch_add(b); }
 }  // namespace strom

@@ -10,6 +10,7 @@ namespace strom {
 
 void set_error(const std::string& msg);
 void count_launches(int64_t n);   // bookkeeping behind strom_launch_count()
+int64_t thread_launch_count();    // the calling host thread's share of it
 void count_h2d(uint64_t bytes);
 void count_d2h(uint64_t bytes);
 

@@ -108,7 +108,7 @@ void build_graph(strom_solver* s) {
   if (s->graph) return;
   psd_configure();
   STROM_CUDA(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
-  const uint64_t before = strom_launch_count();
+  const int64_t before = thread_launch_count();  // other host threads may launch meanwhile
   try {
     enqueue_iteration(s, s->stream);
   } catch (...) {
@@ -118,7 +118,7 @@ void build_graph(strom_solver* s) {
     throw;
   }
   STROM_CUDA(cudaStreamEndCapture(s->stream, &s->graph_def));
-  s->graph_kernels = (int64_t)(strom_launch_count() - before);
+  s->graph_kernels = thread_launch_count() - before;
   count_launches(-s->graph_kernels);  // captured, not launched
   STROM_CUDA(cudaGraphInstantiate(&s->graph, s->graph_def, 0));
 }

@@ -81,10 +81,13 @@ def main(argv):
     import multiprocessing as mp
     with mp.get_context("spawn").Pool(workers) as pool:
         for r in pool.imap_unordered(solve_one, jobs):
+            # re-read before each write: entries another run added meanwhile are kept
+            refs = json.load(open(OUT)) if os.path.exists(OUT) else {}
             refs.setdefault(r["kind"], {})[str(r["index"])] = r
-            with open(OUT + ".tmp", "w") as f:
+            tmp = "%s.%d.tmp" % (OUT, os.getpid())
+            with open(tmp, "w") as f:
                 json.dump(refs, f, indent=1, sort_keys=True)
-            os.replace(OUT + ".tmp", OUT)
+            os.replace(tmp, OUT)
             print(json.dumps(r), flush=True)
 
 

@@ -115,19 +115,25 @@ def test_served_requests_match_oracle():
 
 
 def test_cartpole_batch_of_8_matches_oracle():
-    """Cart-pole N = 50, the 8 seeded instances, one batched solver in mixed
-    precision with the sparse factor of the y-solve and a shared tail."""
+    """Cart-pole N = 50, the seeded instances that have an oracle reference
+    (of the first 8), one batched solver in mixed precision with the sparse
+    factor of the y-solve and a shared tail. Its relaxation is not tight
+    (lambda_2 / lambda_1 about 0.7: not certified, like the oracle's), and
+    at KKT 1e-6 the objective is still about 1e-5 (relative) from the
+    optimum, so this test solves to KKT 1e-7 to hold the 1e-6 objective bar."""
     S = lib()
-    idx = list(range(8))
-    refs = _refs("cartpole", idx)
+    if not os.path.exists(REFS):
+        pytest.skip("no oracle references (tests/golden/make_oracle_refs.py)")
+    have = json.load(open(REFS)).get("cartpole", {})
+    idx = [i for i in range(8) if str(i) in have]
+    if not idx:
+        pytest.skip("no cart-pole oracle references yet")
+    refs = [have[str(i)] for i in idx]
     probs = wl.problem_batch("cartpole", 8, N=50)
-    P = [S.Problem(p) for p in probs]
-    solver = S.Solver([q.relax() for q in P], tol=1e-6, maxiter=30000, precision=S.STROM_PREC_MIXED,
-                      check_every=100, factor=S.STROM_FACTOR_SPARSE)
-    st = solver.solve()
+    P = [S.Problem(probs[i]) for i in idx]
+    solver = S.Solver([q.relax() for q in P], tol=1e-7, maxiter=40000, precision=S.STROM_PREC_MIXED,
+                      polish_eta=1e-6, check_every=100, factor=S.STROM_FACTOR_SPARSE)
+    assert solver.solve() == S.STROM_OK
     certs = solver.certify_batch(P)
-    for i in idx:
-        if not refs[i]["converged"]:
-            continue
-        assert st == S.STROM_OK or solver.result(i).status == S.STROM_OK, i
-        _check(S, solver.result(i), certs[i], refs[i], ("cartpole", i))
+    for k, i in enumerate(idx):
+        _check(S, solver.result(k), certs[k], refs[k], ("cartpole", i))
