@@ -13,6 +13,9 @@ Sets (instance i of a set is workloads.problem_batch(kind, ...)[i]):
   cartpole    N = 50, seeds 0..7 of the cart-pole batch
   rigid_body  the 8 instances of the 128-instance uneven batch
               (N ~ U{20..100}) with the shortest horizons
+  mixed       requests of the seeded serving stream (workloads.mixed_request,
+              keyed by request index): the first 16 pendulum requests and the
+              first 6 cart-pole requests
 
 Usage: python tests/golden/make_oracle_refs.py SET [SET ...] [--workers K]
 Existing entries are kept; only missing ones are computed. Single-threaded BLAS per worker.
@@ -46,6 +49,18 @@ def instances(kind):
         ps = wl.problem_batch("rigid_body", RIGID_BATCH)
         order = sorted(range(len(ps)), key=lambda i: (ps[i].N, i))[:8]
         return [(i, ps[i]) for i in sorted(order)]
+    if kind == "mixed":
+        out, npend, ncart = [], 0, 0
+        for j in range(10000):
+            k, p = wl.mixed_request(j)
+            if k == "pendulum" and npend < 16:
+                out.append((j, p))
+                npend += 1
+            elif k == "cartpole" and ncart < 6:
+                out.append((j, p))
+                ncart += 1
+            if npend == 16 and ncart == 6:
+                return out
     raise ValueError(kind)
 
 
