@@ -47,24 +47,29 @@ def parse():
     ap.add_argument("--slots", type=int, default=1024)
     ap.add_argument("--iters", type=int, default=800, help="sGS-ADMM iterations per step")
     ap.add_argument("--horizon", type=int, default=10)
-    ap.add_argument("--maxiter", type=int, default=6000)
+    ap.add_argument("--maxiter", type=int, default=20000)
     ap.add_argument("--plain", type=int, default=1, help="instances timed in the plain FP64 single-instance form")
     ap.add_argument("--cpu-budget", type=float, default=25.0)
     ap.add_argument("--batch", type=int, default=0, help="cartpole / rigid workloads: instances (0 = 256 / 128)")
     ap.add_argument("--horizon-batch", type=int, default=0,
                     help="cartpole / rigid workloads: horizon (0 = 50 / N ~ U{20..100})")
     ap.add_argument("--check", type=int, default=100, help="cartpole / rigid workloads: iterations between checks")
-    ap.add_argument("--workload", default="served", choices=["served", "psd", "warm", "poisson", "cartpole", "rigid"],
+    ap.add_argument("--workload", default="served", choices=["served", "psd", "warm", "poisson", "cartpole", "rigid",
+                                                           "mixed"],
                     help="served: certified solves/s (default); psd: the 4096-block PSD-projection microbench; "
                          "warm: nearest-neighbour warm starts from a database of solved pendulums; "
                          "poisson: open-loop Poisson arrivals served cold and with warm starts from solved requests")
-    ap.add_argument("--rate", type=float, default=40.0, help="poisson workload: arrivals per second")
+    ap.add_argument("--rate", type=float, default=40.0, help="poisson / mixed workloads: arrivals per second")
+    ap.add_argument("--kinds", default="pendulum,cartpole", help="mixed workload: robots served")
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="mixed workload: device-memory budget")
+    ap.add_argument("--slots-class", type=int, default=64, help="mixed workload: most slots per structure")
+    ap.add_argument("--drain", type=float, default=120.0, help="mixed workload: seconds served after the last arrival")
     ap.add_argument("--duration", type=float, default=12.0, help="poisson workload: seconds of arrivals")
     ap.add_argument("--step-iters", type=int, default=40, help="poisson workload: iterations per serving step")
     ap.add_argument("--warm-grid", type=int, default=9, help="warm workload: database grid points per key axis")
     ap.add_argument("--warm-queries", type=int, default=256, help="warm workload: batched queries")
     ap.add_argument("--warm-single", type=int, default=4, help="warm workload: single-instance FP64 queries")
-    ap.add_argument("--profile", default="none", choices=["none", "iterations", "psd"],
+    ap.add_argument("--profile", default="none", choices=["none", "iterations", "psd", "cartpole"],
                     help="run a few launches of one case and exit (for ncu captures); prints no JSON")
     ap.add_argument("--precision", type=int, default=1, help="psd workload / profile: 0 = FP64, 1 = FP32")
     ap.add_argument("--polish-eta", type=float, default=1e-6,
@@ -357,7 +362,12 @@ def run_strom(a, rank, world):
             "latency_s": {"service_p50": float(np.percentile(svc, 50)), "service_p99": float(np.percentile(svc, 99)),
                           "plain_single_p50": float(np.median(plain_lat)) if plain_lat else None},
             "iterations": {"p50": float(np.percentile(iters, 50)), "p99": float(np.percentile(iters, 99))},
-            "completed": len(finished), "counted": solved, "certified_fraction": cert_frac,
+            "completed": len(finished), "counted": solved,
+            "converged": sum(1 for f in finished if f[0].status == S.STROM_OK),
+            "maxiter_hit": sum(1 for f in finished if f[0].status == S.STROM_MAXITER),
+            "converged_fraction_of_completed": (sum(1 for f in finished if f[0].status == S.STROM_OK)
+                                                / max(1, len(finished))),
+            "certified_fraction": cert_frac,
             "rank1_certified_per_s": verdicts["certified"] / t, "verdicts": verdicts,
             "plain_fp64": plain, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
         }
@@ -540,6 +550,11 @@ def run_profile(a):
         _, sd = feed.take(a.slots)
         sv = S.Solver(sd, tol=1e-6, precision=a.precision, check_every=1)
         sv.step(3)
+    elif a.profile == "cartpole":
+        import workloads as wl
+        _, sd = relax_all(S, wl.problem_batch("cartpole", a.batch or 256, N=a.horizon_batch or 50))
+        sv = S.Solver(sd, tol=1e-6, precision=S.STROM_PREC_MIXED, check_every=10, factor=S.STROM_FACTOR_SPARSE)
+        sv.step(30)
     else:
         import workloads as wl
         x, off, n, _ = wl.psd_microbench()
@@ -938,6 +953,111 @@ def run_poisson(a):
     print(json.dumps(line))
 
 
+def run_mixed(a):
+    """Serving the mixed stream (50% pendulum N ~ U{10..60}, 30% cart-pole
+    N ~ U{20..80}, 20% planar rigid body N ~ U{20..100}; seeded) arriving as a
+    Poisson process of rate --rate for --duration seconds, through one
+    strom_server: one batch per structure class, sized from an HBM byte
+    budget (--budget-gb), idle batches evicted when another structure needs
+    the room, every batch with work stepped at once. --kinds restricts the
+    robots (requests of other robots are dropped from the same stream).
+    Latency = arrival to the host seeing the result, queueing included. The
+    requests that have a stored oracle reference (tests/golden/oracle_refs.json,
+    set "mixed", keyed by request index) are compared with it."""
+    import numpy as np
+    import torch
+    import paper_2406_05846_gb300 as S
+    import workloads as wl
+    S.lib()
+    kinds = set(a.kinds.split(","))
+    arr_all = wl.poisson_arrivals(a.rate, a.duration)
+    reqs = []
+    for j, t in enumerate(arr_all):
+        kind, p = wl.mixed_request(j)
+        if kind in kinds:
+            reqs.append((j, t, kind, p))
+    P, sd = relax_all(S, [r[3] for r in reqs])
+    opts = dict(tol=1e-6, maxiter=a.maxiter, precision=S.STROM_PREC_MIXED, polish_eta=a.polish_eta,
+                check_every=a.step_iters)
+    srv = S.Server(int(a.budget_gb * 1e9), a.slots_class, **opts)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    clk = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    refs = _oracle_refs("mixed")
+    pending, res = {}, {}
+    nxt = 0
+    l0 = S.launch_count()
+    torch.cuda.synchronize()
+    clk.start()
+    t0 = time.perf_counter()
+    limit = a.duration + a.drain
+    while True:
+        now = time.perf_counter() - t0
+        while nxt < len(reqs) and reqs[nxt][1] <= now:
+            pending[srv.submit(sd[nxt], P[nxt])] = nxt
+            nxt += 1
+        if (not pending and nxt >= len(reqs)) or now > limit:
+            break
+        if pending:
+            srv.step(a.step_iters, sp)
+        else:
+            time.sleep(max(0.0, min(0.01, reqs[nxt][1] - now)))
+        done_at = time.perf_counter() - t0
+        for t in list(pending):
+            o = srv.poll(t)
+            if o is not None:
+                k = pending.pop(t)
+                res[k] = (o, done_at - reqs[k][1])
+    span = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    launches = S.launch_count() - l0
+    classes, used = srv.info()
+    per = {}
+    for kind in sorted(kinds):
+        ks = [k for k in range(len(reqs)) if reqs[k][2] == kind]
+        ok = [k for k in ks if k in res and res[k][0][0].status == S.STROM_OK]
+        lat = np.array([res[k][1] for k in ok] or [np.nan])
+        its = np.array([res[k][0][0].iterations for k in ok] or [0])
+        per[kind] = {"arrived": len(ks), "converged": len(ok),
+                     "maxiter": sum(1 for k in ks if k in res and res[k][0][0].status == S.STROM_MAXITER),
+                     "unfinished": sum(1 for k in ks if k not in res),
+                     "certified": sum(1 for k in ok if res[k][0][1] is not None and res[k][0][1].certified),
+                     "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+                     "iterations_p50": float(np.percentile(its, 50))}
+    ok_all = [k for k in res if res[k][0][0].status == S.STROM_OK]
+    lat = np.array([res[k][1] for k in ok_all] or [np.nan])
+    parity = []
+    for k, (j, _, kind, _) in enumerate(reqs):
+        ref = refs.get(str(j))
+        if ref is None or k not in res or not ref.get("converged"):
+            continue
+        r, c = res[k][0][0], res[k][0][1]
+        parity.append({"request": j, "kind": kind, "converged": r.status == S.STROM_OK,
+                       "rel_obj": abs(r.pobj - ref["pobj"]) / (1 + abs(ref["pobj"])),
+                       "certified": bool(c is not None and c.certified), "oracle_certified": ref["certified"]})
+    line = {"metric": "served mixed requests under Poisson arrivals: solves/s, latency (arrival to result)",
+            "value": len(ok_all) / span, "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "higher_is_better": True, "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": "mixed stream (pendulum N~U{10..60} 50%%, cart-pole N~U{20..80} 30%%, rigid body "
+                                   "N~U{20..100} 20%%; robots served: %s), Poisson %.1f/s for %.0f s, %d requests "
+                                   "served, budget %.0f GB, at most %d slots per structure, %d iterations per step, "
+                                   "KKT<=1e-6, certificate per request" %
+                                   (",".join(sorted(kinds)), a.rate, a.duration, len(reqs), a.budget_gb,
+                                    a.slots_class, a.step_iters)},
+            "span_s": span, "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "per_robot": per, "classes": len(classes), "budget_used_gb": used / 1e9,
+            "batches_created": sum(c["batches_created"] for c in classes), "gpu_launches": launches,
+            "oracle_parity": {"sampled": len(parity),
+                              "objective_within_1e-6": sum(p["rel_obj"] <= 1e-6 for p in parity if p["converged"]),
+                              "verdicts_equal": sum(p["certified"] == p["oracle_certified"] for p in parity),
+                              "pass_rate": (sum(p["converged"] and p["certified"] == p["oracle_certified"]
+                                                for p in parity) / len(parity)) if parity else None,
+                              "cases": parity},
+            "clocks": clocks}
+    print(json.dumps(line))
+
+
 def main():
     a = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -957,6 +1077,8 @@ def main():
         run_poisson(a)
     elif a.workload in ("cartpole", "rigid"):
         run_batch(a)
+    elif a.workload == "mixed":
+        run_mixed(a)
     else:
         run_strom(a, rank, world)
 

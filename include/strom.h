@@ -528,14 +528,27 @@ int strom_kernel_solve(const strom_solver* s, const double* r_dev, double* y_dev
  * solver's stream; the fastest is kept for every later iteration (the
  * captured iteration graph is rebuilt on the next step). Without a shared
  * tail only the one-instance-per-CTA solve exists and nothing changes.
+ * Then the eigensolver: each block-size class's launch is timed with each
+ * of its thread counts (2 or 3 per class), in each precision the solver
+ * uses, and the fastest is kept. The thread count changes only which
+ * thread updates which entries, and the order in which the off-diagonal
+ * sum of the stopping test is added up, so results agree to rounding.
  * The solver's state (X, S, y, sigma) is not touched. reps in 1..1000.
- * Allocates two scratch vectors of m_total doubles for the duration of the
- * call. Waits for `stream` (may be NULL) before timing. */
+ * Allocates two scratch vectors of m_total doubles and two of nsvec_total
+ * doubles for the duration of the call. Waits for `stream` (may be NULL)
+ * before timing. */
 typedef struct {
   int32_t ncand;             /* candidates timed */
   int32_t tile[4];           /* instances per CTA of each candidate */
   double ms[4];              /* mean time of one y-solve (milliseconds) */
   int32_t chosen;            /* tile kept */
+  /* eigensolver: per precision ([0] FP64, [1] FP32, the latter only when the
+   * solver uses it) and block-size class (n <= 16, 40, 80, 160), the threads
+   * per CTA kept (0: no blocks in the class) and the mean time of that
+   * class's launch with them (cold sweeps on a fixed pseudo-random input of
+   * the solver's block layout) */
+  int32_t eig_threads[2][4];
+  double eig_ms[2][4];
 } strom_tune_report;
 int strom_solver_tune(strom_solver* s, int32_t reps, void* stream, strom_tune_report* out);
 

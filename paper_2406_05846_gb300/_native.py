@@ -91,7 +91,8 @@ class strom_server_class(C.Structure):
 
 
 class strom_tune_report(C.Structure):
-    _fields_ = [("ncand", C.c_int32), ("tile", C.c_int32 * 4), ("ms", C.c_double * 4), ("chosen", C.c_int32)]
+    _fields_ = [("ncand", C.c_int32), ("tile", C.c_int32 * 4), ("ms", C.c_double * 4), ("chosen", C.c_int32),
+                ("eig_threads", (C.c_int32 * 4) * 2), ("eig_ms", (C.c_double * 4) * 2)]
 
 
 SIGNATURES = {

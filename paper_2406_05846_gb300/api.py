@@ -335,10 +335,15 @@ class Solver:
         check(lib().strom_kernel_solve(self.handle, r_ptr, y_ptr, stream), "strom_kernel_solve")
 
     def tune(self, reps=5, stream=None):
-        """strom_solver_tune: time the y-solve launch shapes and keep the fastest.
-        Returns ({tile: ms per y-solve}, chosen tile)."""
+        """strom_solver_tune: time the y-solve launch shapes and the eigensolver's
+        threads per CTA, keep the fastest. Returns ({tile: ms per y-solve},
+        chosen tile); the eigensolver's choices are in self.eig_tuning
+        ({precision: {size class: (threads, ms)}})."""
         rep = N.strom_tune_report()
         check(lib().strom_solver_tune(self.handle, int(reps), stream, C.byref(rep)), "strom_solver_tune")
+        self.eig_tuning = {("fp64", "fp32")[p]: {k: (rep.eig_threads[p][k], rep.eig_ms[p][k])
+                                                 for k in range(4) if rep.eig_threads[p][k] > 0}
+                           for p in range(2)}
         return {rep.tile[i]: rep.ms[i] for i in range(rep.ncand)}, rep.chosen
 
 

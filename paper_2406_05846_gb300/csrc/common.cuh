@@ -105,7 +105,17 @@ struct PsdClasses {
   int count[4] = {0, 0, 0, 0};
   int start[4] = {0, 0, 0, 0};
   int max_n[4] = {0, 0, 0, 0};
+  // threads per CTA of each class's launch, [0] FP64 / [1] FP32; 0 = the
+  // default shape (psd_threads_candidates lists the others)
+  int threads[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
 };
+
+// launch shapes (threads per CTA) of size class k in one precision; the first
+// is the default. Returns how many (at most 3).
+int psd_threads_candidates(int precision, int k, int* out);
+// a deterministic symmetric test input (svec entries in [-1, 1] from a hash
+// of the index), for timing the eigensolver's launch shapes
+void psd_fill_test_input(double* x, int64_t n, cudaStream_t st);
 
 // doubles of global scratch per FP64 block of the n <= 160 class (V^T, 160 x 162)
 constexpr size_t kVScratchPerBlock = 160 * 162;

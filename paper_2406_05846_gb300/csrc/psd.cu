@@ -47,6 +47,16 @@ __device__ double block_sum(double v, double* red) {
   return s;
 }
 
+template <typename T> struct Vec2;
+template <> struct Vec2<float> {
+  using type = float2;
+  static __device__ __forceinline__ float2 make(float a, float b) { return make_float2(a, b); }
+};
+template <> struct Vec2<double> {
+  using type = double2;
+  static __device__ __forceinline__ double2 make(double a, double b) { return make_double2(a, b); }
+};
+
 template <typename T> struct Vec;
 template <> struct Vec<float> { using type = float4; static constexpr int W = 4; };
 template <> struct Vec<double> { using type = double2; static constexpr int W = 2; };
@@ -83,11 +93,11 @@ __global__ void __launch_bounds__(NT) jacobi_psd_kernel(PsdArgs a, int list_star
   T* A = reinterpret_cast<T*>(smem_raw);
   T* V = VSMEM ? reinterpret_cast<T*>(smem_raw + SM::a_bytes)
                : reinterpret_cast<T*>(a.vscratch) + (size_t)blockIdx.x * NP * LDV;
-  T* sT = reinterpret_cast<T*>(smem_raw + SM::a_bytes + SM::v_bytes);
-  T* sS = sT + SM::H;
-  T* sU = sS + SM::H;
-  int* sP = reinterpret_cast<int*>(sU + SM::H);
-  int* sQ = sP + SM::H;
+  // rotation of pair t: (s, tau) together, (p, q) together, one load each
+  using T2 = typename Vec2<T>::type;
+  T2* sSU = reinterpret_cast<T2*>(smem_raw + SM::a_bytes + SM::v_bytes);
+  int2* sPQ = reinterpret_cast<int2*>(sSU + SM::H);
+  T* sT = reinterpret_cast<T*>(sPQ + SM::H);
   double* red = reinterpret_cast<double*>(smem_raw + SM::a_bytes + SM::v_bytes + SM::rot_bytes + 16);
   red = reinterpret_cast<double*>((reinterpret_cast<uintptr_t>(red) + 7) & ~uintptr_t(7));
   T* Tm = reinterpret_cast<T*>(smem_raw + ((SM::a_bytes + SM::v_bytes + SM::rot_bytes + SM::red_bytes + 16 + 15) / 16) * 16);
@@ -230,7 +240,9 @@ __global__ void __launch_bounds__(NT) jacobi_psd_kernel(PsdArgs a, int list_star
           s = tt * c;
           ta = s / (T(1) + c);
         }
-        sP[t] = p; sQ[t] = q; sT[t] = tt; sS[t] = s; sU[t] = ta;
+        sPQ[t] = make_int2(p, q);
+        sT[t] = tt;
+        sSU[t] = Vec2<T>::make(s, ta);
       }
       __syncthreads();
 #pragma unroll
@@ -238,7 +250,8 @@ __global__ void __launch_bounds__(NT) jacobi_psd_kernel(PsdArgs a, int list_star
         const uint32_t code = itA[i];
         if (code == 0xffffffffu) continue;
         const int t1 = (int)(code >> 16), t2 = (int)(code & 0xffffu);
-        const int p1 = sP[t1], q1 = sQ[t1], p2 = sP[t2], q2 = sQ[t2];
+        const int2 pq1 = sPQ[t1], pq2 = sPQ[t2];
+        const int p1 = pq1.x, q1 = pq1.y, p2 = pq2.x, q2 = pq2.y;
         const T x00 = A[p1 * LD + p2], x01 = A[p1 * LD + q2];
         const T x10 = A[q1 * LD + p2], x11 = A[q1 * LD + q2];
         if (t1 == t2) {
@@ -251,7 +264,8 @@ __global__ void __launch_bounds__(NT) jacobi_psd_kernel(PsdArgs a, int list_star
         } else {
           // J1^T X J2 written as corrections x - s (y + tau x) (Rutishauser):
           // no rounding bias from c ~ 1 when the rotation is small
-          const T s1 = sS[t1], u1 = sU[t1], s2 = sS[t2], u2 = sU[t2];
+          const T2 su1 = sSU[t1], su2 = sSU[t2];
+          const T s1 = su1.x, u1 = su1.y, s2 = su2.x, u2 = su2.y;
           const T r00 = x00 - s1 * (x10 + u1 * x00), r10 = x10 + s1 * (x00 - u1 * x10);
           const T r01 = x01 - s1 * (x11 + u1 * x01), r11 = x11 + s1 * (x01 - u1 * x11);
           const T y00 = r00 - s2 * (r01 + u2 * r00);
@@ -269,8 +283,10 @@ __global__ void __launch_bounds__(NT) jacobi_psd_kernel(PsdArgs a, int list_star
         const uint32_t code = itV[i];
         if (code == 0xffffffffu) continue;
         const int t = (int)(code >> 16), c = (int)(code & 0xffffu);
-        const int p = sP[t], q = sQ[t];
-        const T s = sS[t], u = sU[t];
+        const int2 pq = sPQ[t];
+        const int p = pq.x, q = pq.y;
+        const T2 su = sSU[t];
+        const T s = su.x, u = su.y;
         VT* vp = reinterpret_cast<VT*>(V + p * LDV) + c;
         VT* vq = reinterpret_cast<VT*>(V + q * LDV) + c;
         VT a4 = *vp, b4 = *vq;
@@ -382,6 +398,55 @@ void launch_class(const PsdArgs& a, int start, int count, double tol, int sweeps
 
 }  // namespace
 
+namespace {
+
+// Launch shapes per size class: the block size of a class is fixed by its
+// shared-memory layout (NP); the thread count is a free choice (more threads:
+// fewer 2x2 updates each, fewer CTAs per SM). The first entry is the default.
+constexpr int kThr64[4][3] = {{64, 32, 0}, {128, 64, 256}, {256, 128, 512}, {512, 256, 0}};
+constexpr int kThr32[4][3] = {{64, 32, 0}, {128, 64, 256}, {256, 128, 512}, {512, 256, 0}};
+
+template <typename T, int NP, bool VSMEM, int NT0, int NT1, int NT2>
+void set_attrs() {
+  set_attr<T, NP, NT0, VSMEM>();
+  set_attr<T, NP, NT1, VSMEM>();
+  if constexpr (NT2 > 0) set_attr<T, NP, NT2, VSMEM>();
+}
+
+template <typename T, int NP, bool VSMEM, int NT0, int NT1, int NT2>
+void launch_sel(int threads, const PsdArgs& a, int start, int count, double tol, int sweeps, cudaStream_t st) {
+  if (threads == NT1) launch_class<T, NP, NT1, VSMEM>(a, start, count, tol, sweeps, st);
+  else if (NT2 > 0 && threads == NT2) launch_class<T, NP, (NT2 > 0 ? NT2 : NT0), VSMEM>(a, start, count, tol, sweeps, st);
+  else launch_class<T, NP, NT0, VSMEM>(a, start, count, tol, sweeps, st);
+}
+
+__global__ void fill_test_kernel(double* x, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t h = (uint64_t)i * 0x9E3779B97F4A7C15ull;
+    h ^= h >> 31;
+    h *= 0xBF58476D1CE4E5B9ull;
+    h ^= h >> 29;
+    x[i] = (double)(h >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+  }
+}
+
+}  // namespace
+
+int psd_threads_candidates(int precision, int k, int* out) {
+  const int(*t)[3] = precision == STROM_PREC_FP64 ? kThr64 : kThr32;
+  int c = 0;
+  for (int j = 0; j < 3; ++j)
+    if (t[k][j] > 0) out[c++] = t[k][j];
+  return c;
+}
+
+void psd_fill_test_input(double* x, int64_t n, cudaStream_t st) {
+  if (n <= 0) return;
+  fill_test_kernel<<<(int)std::min<int64_t>(4096, (n + 255) / 256), 256, 0, st>>>(x, n);
+  STROM_CUDA(cudaGetLastError());
+  count_launches(1);
+}
+
 // The shared-memory attributes are per device: each device is configured once,
 // under a lock so that host threads calling at the same time do not race.
 void psd_configure() {
@@ -393,14 +458,14 @@ void psd_configure() {
   if (dev < 0 || dev >= kMaxDev) throw StatusError(STROM_ERR_INVALID, "psd_configure: device index out of range");
   std::lock_guard<std::mutex> lk(mu);
   if (done[dev]) return;
-  set_attr<double, 16, 64, true>();
-  set_attr<double, 40, 128, true>();
-  set_attr<double, 80, 256, true>();
-  set_attr<double, 160, 512, false>();
-  set_attr<float, 16, 64, true>();
-  set_attr<float, 40, 128, true>();
-  set_attr<float, 80, 256, true>();
-  set_attr<float, 160, 512, true>();
+  set_attrs<double, 16, true, 64, 32, 0>();
+  set_attrs<double, 40, true, 128, 64, 256>();
+  set_attrs<double, 80, true, 256, 128, 512>();
+  set_attrs<double, 160, false, 512, 256, 0>();
+  set_attrs<float, 16, true, 64, 32, 0>();
+  set_attrs<float, 40, true, 128, 64, 256>();
+  set_attrs<float, 80, true, 256, 128, 512>();
+  set_attrs<float, 160, true, 512, 256, 0>();
   done[dev] = true;
 }
 
@@ -409,17 +474,19 @@ void psd_launch(const PsdArgs& a, const PsdClasses& c, int precision, cudaStream
   if (precision == STROM_PREC_FP64) {
     const double tol = 1e-14;
     const int sw = 30;
-    launch_class<double, 16, 64, true>(a, c.start[0], c.count[0], tol, sw, st);
-    launch_class<double, 40, 128, true>(a, c.start[1], c.count[1], tol, sw, st);
-    launch_class<double, 80, 256, true>(a, c.start[2], c.count[2], tol, sw, st);
-    launch_class<double, 160, 512, false>(a, c.start[3], c.count[3], tol, sw, st);
+    const int* th = c.threads[0];
+    launch_sel<double, 16, true, 64, 32, 0>(th[0], a, c.start[0], c.count[0], tol, sw, st);
+    launch_sel<double, 40, true, 128, 64, 256>(th[1], a, c.start[1], c.count[1], tol, sw, st);
+    launch_sel<double, 80, true, 256, 128, 512>(th[2], a, c.start[2], c.count[2], tol, sw, st);
+    launch_sel<double, 160, false, 512, 256, 0>(th[3], a, c.start[3], c.count[3], tol, sw, st);
   } else {
     const double tol = 2e-6;
     const int sw = 20;
-    launch_class<float, 16, 64, true>(a, c.start[0], c.count[0], tol, sw, st);
-    launch_class<float, 40, 128, true>(a, c.start[1], c.count[1], tol, sw, st);
-    launch_class<float, 80, 256, true>(a, c.start[2], c.count[2], tol, sw, st);
-    launch_class<float, 160, 512, true>(a, c.start[3], c.count[3], tol, sw, st);
+    const int* th = c.threads[1];
+    launch_sel<float, 16, true, 64, 32, 0>(th[0], a, c.start[0], c.count[0], tol, sw, st);
+    launch_sel<float, 40, true, 128, 64, 256>(th[1], a, c.start[1], c.count[1], tol, sw, st);
+    launch_sel<float, 80, true, 256, 128, 512>(th[2], a, c.start[2], c.count[2], tol, sw, st);
+    launch_sel<float, 160, true, 512, 256, 0>(th[3], a, c.start[3], c.count[3], tol, sw, st);
   }
 }
 

@@ -1007,7 +1007,50 @@ extern "C" int strom_solver_tune(strom_solver* s, int32_t reps, void* stream, st
     if (!sparse) s->yd.tile_r = best;
     out->ncand = (int32_t)cand.size();
     out->chosen = best;
-    if (best != old_tile) {
+    // eigensolver launch shapes: each size class alone, each candidate
+    // thread count, cold sweeps on a fixed pseudo-random input of the
+    // solver's block layout (the state is not touched)
+    bool eig_changed = false;
+    {
+      DevBuf<double> xin, xout;
+      xin.alloc(s->nsvec);
+      xout.alloc(s->nsvec);
+      psd_fill_test_input(xin.p, s->nsvec, st);
+      const int precs[2] = {STROM_PREC_FP64, STROM_PREC_FP32};
+      for (int pi = 0; pi < 2; ++pi) {
+        if (precs[pi] == STROM_PREC_FP32 && s->opt.precision == STROM_PREC_FP64) continue;
+        for (int k = 0; k < 4; ++k) {
+          if (s->cls.count[k] == 0) continue;
+          int cands[3];
+          const int nc = psd_threads_candidates(precs[pi], k, cands);
+          PsdClasses one{};
+          one.start[k] = s->cls.start[k];
+          one.count[k] = s->cls.count[k];
+          one.max_n[k] = s->cls.max_n[k];
+          PsdArgs a = psd_args(s, xin.p, xout.p, nullptr, false);
+          double bms = -1.0;
+          int bth = cands[0];
+          for (int c = 0; c < nc; ++c) {
+            one.threads[pi][k] = cands[c];
+            psd_launch(a, one, precs[pi], st);  // warm-up
+            STROM_CUDA(cudaEventRecord(ev.a, st));
+            for (int r = 0; r < reps; ++r) psd_launch(a, one, precs[pi], st);
+            STROM_CUDA(cudaEventRecord(ev.b, st));
+            STROM_CUDA(cudaEventSynchronize(ev.b));
+            float ms = 0.0f;
+            STROM_CUDA(cudaEventElapsedTime(&ms, ev.a, ev.b));
+            const double m = (double)ms / reps;
+            if (bms < 0.0 || m < bms) { bms = m; bth = cands[c]; }
+          }
+          const int old = s->cls.threads[pi][k] ? s->cls.threads[pi][k] : cands[0];
+          if (bth != old) eig_changed = true;
+          s->cls.threads[pi][k] = bth;
+          out->eig_threads[pi][k] = bth;
+          out->eig_ms[pi][k] = bms;
+        }
+      }
+    }
+    if (best != old_tile || eig_changed) {
       // the captured iteration holds the old launch shape: capture again on the next step
       if (s->graph) { STROM_CUDA(cudaGraphExecDestroy(s->graph)); s->graph = nullptr; }
       if (s->graph_def) { STROM_CUDA(cudaGraphDestroy(s->graph_def)); s->graph_def = nullptr; }

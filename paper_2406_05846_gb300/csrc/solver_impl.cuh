@@ -18,7 +18,7 @@ namespace strom {
 // factorisations when several patterns would not fit together
 struct SpPatHost {
   std::unique_ptr<SpSymbolic> sym;
-  DevBuf<int64_t> fptr, bptr, fsplit, bsplit;
+  DevBuf<int64_t> fptr, bptr, fsplit, bsplit, fgrp, bgrp;
   DevBuf<int32_t> fcol, brow, grp_ptr, blk_grp, can_local;
   DevBuf<int64_t> s_dst;
   DevBuf<int32_t> fmap, s_ri, s_rj;

@@ -224,17 +224,25 @@ __global__ void __launch_bounds__(BINV_W * 32) sp_blockinv_kernel(SpDev d, const
 // only its own group and the group before it (forward), a column only its
 // own group and the group after it (backward). Inside a group the positions
 // are taken a block of 32 at a time:
-//  forward  (L w = t):   each row of the block subtracts its entries in earlier
-//                        blocks (8 lanes per row, a fixed 3-step sum), then the
-//                        block is solved through the inverse of its diagonal
-//                        part (one thread per output, no cross-lane sum)
-//  backward (L^T y = w): the same with the columns' entries in later blocks and
-//                        the transposed inverse, blocks and groups last to first
+//  forward  (L w = t):   when a group starts, every row subtracts its entries
+//                        in the previous group (all rows at once, 8 lanes per
+//                        row); then block by block, each row of the block
+//                        subtracts its entries in earlier blocks of its group
+//                        (8 lanes per row, a fixed 3-step sum), and the block
+//                        is solved through the inverse of its diagonal part
+//                        (one thread per output, four partial sums)
+//  backward (L^T y = w): the same with the columns' entries in the next group
+//                        and in later blocks, and the transposed inverse,
+//                        blocks and groups last to first
 // The entries a step needs do not depend on the solution, so each step loads
-// the next step's first entries, its rows' entry ranges two steps ahead, and
+// the next step's first entries (up to 32 of a row), its rows' entry ranges
+// two steps ahead, and
 // its block inverse while the current step computes: a step waits on shared
 // memory and on the FP64 pipe, not on global memory. Two barriers a step.
-constexpr int SP_PF = 4;        // entries per lane loaded a step ahead
+// entries per lane loaded a step ahead: 4 (32 entries of a row) for up to
+// four right-hand sides per CTA, 2 for eight (registers); the per-lane
+// order of the entries, and so the arithmetic, is the same for every choice
+template <int R> struct SpPf { static constexpr int value = R <= 4 ? 4 : 2; };
 constexpr int SP_MAXG = kSpMaxGroups;
 
 // walks the blocks of a pass in order (forward: first to last, backward: last
@@ -266,7 +274,7 @@ struct BlkIt {
 // one pass of the substitution (FWD: L w = t; otherwise L^T y = w), in place
 // in the group buffers; see sp_solve_kernel
 template <int R, bool FWD>
-__device__ void sp_pass(const SpDev& d, const SpPatDev& P, const SpInstDev* sI, const int* s_act, int i0,
+__device__ void sp_pass_impl(const SpDev& d, const SpPatDev& P, const SpInstDev* sI, const int* s_act, int i0,
                         const int* sg, const int* sb, double* sh, double (*tb)[kSpBlock], double* __restrict__ yout) {
   constexpr int BS = kSpBlock;
   const int tid = threadIdx.x;
@@ -275,14 +283,19 @@ __device__ void sp_pass(const SpDev& d, const SpPatDev& P, const SpInstDev* sI, 
   auto buf = [&](int g, int r) -> double* { return sh + ((size_t)(g & 1) * R + r) * MG; };
   const int q = tid >> 3, l8 = tid & 7;     // gather: row / column q of the block, 8 lanes each
   const int oj = tid % BS, orr = tid / BS;  // block inverse: output oj of instance orr
-  const int64_t* segb = FWD ? P.fptr : P.bsplit;  // entries of row / column p: [segb[p], sege[p])
-  const int64_t* sege = FWD ? P.fsplit : P.bptr + 1;
+  // entries of row / column p inside its group, in earlier blocks: [segb[p], sege[p])
+  const int64_t* segb = FWD ? P.fgrp : P.bsplit;
+  const int64_t* sege = FWD ? P.fsplit : P.bgrp;
+  // entries in the group processed before this one: [cpb[p], cpe[p])
+  const int64_t* cpb = FWD ? P.fptr : P.bgrp;
+  const int64_t* cpe = FWD ? P.fgrp : P.bptr + 1;
   const int32_t* idx = FWD ? P.fcol : P.brow;
   // value table of a row (forward: placed by row) / column (backward)
   auto vals = [&](int r, int p) -> const double* {
     const SpInstDev& I = sI[r];
     return FWD ? d.fval + ((p < nt) ? I.f_tail : I.f_own) : d.bval + ((p < nt) ? I.b_tail : I.b_own);
   };
+  constexpr int SP_PF = SpPf<R>::value;
   BlkIt itk, it1, it2;
   itk.first(sg, sb, G, FWD);
   it1 = itk; it1.next(sg, sb, G, FWD);
@@ -342,6 +355,36 @@ __device__ void sp_pass(const SpDev& d, const SpPatDev& P, const SpInstDev* sI, 
         buf(g, r)[i] = d.w[sI[r].w_off + a + i];
       }
       __syncthreads();
+      // the coupling with the group processed before (its values are final):
+      // every row of this group at once, 8 lanes a row, many loads in flight
+      // instead of one block step's rows at a time
+      if (g != (FWD ? 0 : G - 1)) {
+        const int off_prev = FWD ? pa : b;
+        for (int p0 = a; p0 < b; p0 += SOLVE_T / 8) {
+          const int p = p0 + q;
+          double cacc[R];
+#pragma unroll
+          for (int r = 0; r < R; ++r) cacc[r] = 0.0;
+          if (p < b) {
+            const int64_t e1 = cpe[p];
+#pragma unroll 4
+            for (int64_t e = cpb[p] + l8; e < e1; e += 8) {
+              const int j = idx[e] - off_prev;
+#pragma unroll
+              for (int r = 0; r < R; ++r) cacc[r] += vals(r, p)[e] * buf(g + 1, r)[j];
+            }
+          }
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            double v = cacc[r];
+            v += __shfl_xor_sync(0xffffffffu, v, 4);
+            v += __shfl_xor_sync(0xffffffffu, v, 2);
+            v += __shfl_xor_sync(0xffffffffu, v, 1);
+            if (p < b && l8 == 0) buf(g, r)[p - a] -= v;
+          }
+        }
+        __syncthreads();
+      }
     }
     load_range(it2, nn_e, nn_end);
     const int b0 = itk.b0, bs = itk.bs;
@@ -386,10 +429,12 @@ __device__ void sp_pass(const SpDev& d, const SpPatDev& P, const SpInstDev* sI, 
     __syncthreads();
     // the block through the inverse of its diagonal part
     if (orr < R && oj < bs) {
-      double out = 0.0;
+      // four partial sums (t mod 4), then (s0 + s1) + (s2 + s3): a short
+      // dependency chain, the same order for every tile size
+      double o4[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-      for (int t = 0; t < BS; ++t) out += (t < bs) ? dv[t] * tb[orr][t] : 0.0;
-      buf(g, orr)[b0 - a + oj] = out;
+      for (int t = 0; t < BS; ++t) o4[t & 3] += (t < bs) ? dv[t] * tb[orr][t] : 0.0;
+      buf(g, orr)[b0 - a + oj] = (o4[0] + o4[1]) + (o4[2] + o4[3]);
     }
     load_inverse(it1);
     __syncthreads();
@@ -430,8 +475,8 @@ __global__ void __launch_bounds__(SOLVE_T) sp_solve_kernel(SpDev d, double* __re
     sb[t] = P.blk_grp[t];
   }
   __syncthreads();
-  sp_pass<R, true>(d, P, sI, s_act, i0, sg, sb, sh, tb, yout);
-  sp_pass<R, false>(d, P, sI, s_act, i0, sg, sb, sh, tb, yout);
+  sp_pass_impl<R, true>(d, P, sI, s_act, i0, sg, sb, sh, tb, yout);
+  sp_pass_impl<R, false>(d, P, sI, s_act, i0, sg, sb, sh, tb, yout);
 }
 
 size_t factor_smem(const SpDev& d, int nw) {

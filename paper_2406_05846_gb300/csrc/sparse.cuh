@@ -24,6 +24,8 @@ struct SpPatDev {
   const int32_t* can_local;  // [n] instance-local row id of each position
   const int64_t* fsplit;     // [n] row i: entries in earlier blocks are [fptr[i], fsplit[i])
   const int64_t* bsplit;     // [n] column j: entries in later blocks are [bsplit[j], bptr[j + 1])
+  const int64_t* fgrp;       // [n] row i: entries in the previous group are [fptr[i], fgrp[i])
+  const int64_t* bgrp;       // [n] column j: entries in the next group are [bgrp[j], bptr[j + 1])
   const int32_t* blk_grp;    // [ngroups + 1] first block of each group
   int32_t nblk, tail_blk;    // blocks; blocks of the tail groups
   // factorisation only (device copies exist while a factorisation runs)

@@ -56,6 +56,11 @@ struct SpSymbolic {
   // fsplit[i])); those of column j in rows of later blocks come last
   // ([bsplit[j], bptr[j + 1])); the rest form the block's dense diagonal part.
   std::vector<int64_t> fsplit, bsplit;  // [n]
+  // entries of row i in columns of the previous group (in elimination order)
+  // are [fptr[i], fgrp[i]); entries of column j in rows of the next group
+  // are [bgrp[j], bptr[j + 1]) (the substitution gathers them at once when
+  // a group starts, not block by block)
+  std::vector<int64_t> fgrp, bgrp;      // [n]
   std::vector<int32_t> blk_grp;         // [ngroups + 1] first block of each group
   int32_t nblk = 0;
   int64_t nnz_tail_b = 0;  // column entries of tail columns (they come first)

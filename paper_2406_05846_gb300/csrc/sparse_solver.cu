@@ -31,6 +31,8 @@ void upload_solve_arrays(SpPatHost& P, cudaStream_t st) {
   }
   P.fsplit.upload(y.fsplit.data(), y.fsplit.size(), st);
   P.bsplit.upload(y.bsplit.data(), y.bsplit.size(), st);
+  P.fgrp.upload(y.fgrp.data(), y.fgrp.size(), st);
+  P.bgrp.upload(y.bgrp.data(), y.bgrp.size(), st);
   P.grp_ptr.upload(y.grp_ptr.data(), y.grp_ptr.size(), st);
   P.blk_grp.upload(y.blk_grp.data(), y.blk_grp.size(), st);
   P.can_local.upload(y.can_local.data(), y.can_local.size(), st);
@@ -71,7 +73,8 @@ void refresh_pattern_views(strom_solver* s) {
     SpPatDev v{};
     v.n = y.n; v.n_tail = y.n_tail; v.ngroups = y.ngroups; v.max_group = y.max_group;
     v.fptr = P.fptr.p; v.fcol = P.fcol.p; v.bptr = P.bptr.p; v.brow = P.brow.p; v.grp_ptr = P.grp_ptr.p;
-    v.can_local = P.can_local.p; v.fsplit = P.fsplit.p; v.bsplit = P.bsplit.p; v.blk_grp = P.blk_grp.p;
+    v.can_local = P.can_local.p; v.fsplit = P.fsplit.p; v.bsplit = P.bsplit.p;
+    v.fgrp = P.fgrp.p; v.bgrp = P.bgrp.p; v.blk_grp = P.blk_grp.p;
     v.nblk = y.nblk; v.tail_blk = y.blk_grp[y.ngroups - 1];
     v.fmap = P.fmap.p; v.s_ri = P.s_ri.p; v.s_rj = P.s_rj.p; v.s_dst = P.s_dst.p;
     v.ns = (int64_t)y.s_dst.size(); v.ns_tail = y.ns_tail;

@@ -152,17 +152,23 @@ SpSymbolic* sparse_symbolic(const Sdp& q) {
   s->blk_grp.assign(1, 0);
   s->fsplit.resize(n);
   s->bsplit.resize(n);
+  s->fgrp.resize(n);
+  s->bgrp.resize(n);
   for (int g = 0; g < N; ++g) {
     const int a = s->grp_ptr[g], b = s->grp_ptr[g + 1];
     for (int p = a; p < b; ++p) {
       const int b0 = a + ((p - a) / kSpBlock) * kSpBlock;
       const int b1 = std::min(b, b0 + kSpBlock);
       int64_t e = s->fptr[p];
+      while (e < s->fptr[p + 1] && s->fcol[e] < a) ++e;
+      s->fgrp[p] = e;
       while (e < s->fptr[p + 1] && s->fcol[e] < b0) ++e;
       s->fsplit[p] = e;
       int64_t f = s->bptr[p];
       while (f < s->bptr[p + 1] && s->brow[f] < b1) ++f;
       s->bsplit[p] = f;
+      while (f < s->bptr[p + 1] && s->brow[f] < b) ++f;
+      s->bgrp[p] = f;
     }
     s->blk_grp.push_back(s->blk_grp.back() + (b - a + kSpBlock - 1) / kSpBlock);
   }

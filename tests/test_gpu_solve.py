@@ -133,3 +133,26 @@ def test_batch_iterations_are_repeatable():
         xa, sa, ya = a.state(i)
         xb, sb, yb = b.state(i)
         assert np.array_equal(xa, xb) and np.array_equal(sa, sb) and np.array_equal(ya, yb), i
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_paper_pendulum_matches_oracle(precision):
+    """The paper's own pendulum model (variational integrator on SO(2),
+    9-variable cliques: 55 x 55 moment and 10 x 10 localizing blocks) at
+    N = 5: objective against the oracle run to 1e-8 and the same
+    certificate verdict (rank 1, certified by the oracle)."""
+    S = lib()
+    p = wl.paper_pendulum_problem(N=5, theta0=0.3, thetadot0=0.7)
+    red, ref = oracle_ref(p, ("paper_pend5", 0.3, 0.7))
+    oc = OC.certify(p, red, ref.X, ref.y)
+    P = S.Problem(p)
+    prec = S.STROM_PREC_FP64 if precision == "fp64" else S.STROM_PREC_MIXED
+    solver = S.Solver([P.relax()], tol=1e-6, maxiter=20000, precision=prec, check_every=10)
+    assert solver.solve() == S.STROM_OK
+    r = solver.result(0)
+    assert ref.converged and max(r.eta_p, r.eta_d, r.eta_g) <= 1e-6
+    assert abs(r.pobj - ref.pobj) / (1 + abs(ref.pobj)) <= 1e-6
+    assert np.array_equal(solver.kept_rows(0), red.keep)
+    c = solver.certify(0, P)
+    assert oc.certified and c.rank_one == oc.rank_one and c.certified == oc.certified
+    assert abs(c.phat - oc.phat) <= 1e-5 * (1 + abs(oc.phat))

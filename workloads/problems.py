@@ -317,6 +317,41 @@ def problem_batch(kind: str, B: int, seed: int = BASE_SEED, **kw):
 
 
 # --------------------------------------------------------------------------
+# the serving mix: robots and horizons drawn per request
+# --------------------------------------------------------------------------
+SERVING_MIX = (("pendulum", 0.5, (10, 60)), ("cartpole", 0.3, (20, 80)), ("rigid_body", 0.2, (20, 100)))
+SERVING_SEED = BASE_SEED + 5_000_000
+
+
+def mixed_request(j: int, seed: int = SERVING_SEED):
+    """Request j of the serving stream: its robot is drawn with the shares of
+    SERVING_MIX, its horizon uniformly from the robot's range, then its
+    initial state (and for the rigid body its goal and 2-4 disks) as in
+    problem_batch. Seeded by PCG64(seed + j). Returns (kind, problem)."""
+    rng = np.random.default_rng(np.random.PCG64(seed + j))
+    u = rng.uniform()
+    acc = 0.0
+    for kind, share, (lo, hi) in SERVING_MIX:
+        acc += share
+        if u < acc:
+            break
+    N = int(rng.integers(lo, hi + 1))
+    sub = int(rng.integers(0, 2**31 - 1))
+    return kind, problem_batch(kind, 1, seed=sub, N=N)[0]
+
+
+def poisson_arrivals(rate: float, duration: float, seed: int = SERVING_SEED + 1):
+    """Arrival times (s) of a Poisson process of the given rate on [0, duration)."""
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= duration:
+            return np.array(out)
+        out.append(t)
+
+
+# --------------------------------------------------------------------------
 # the paper's vehicle landing and flying robot (App. "Vehicle Landing",
 # "Flying Robot"): state x = (r_x, r_y, v_x, v_y, r_c, r_s, f_c, f_s),
 # attitude and its step rotation on SO(2) as in the paper's pendulum
