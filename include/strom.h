@@ -39,10 +39,11 @@ enum {
 /* factorisations of the y-solve's Schur complement (strom_options.factor).
  * DENSE: one dense lower triangle per clique and a dense coupling block
  * (blocked substitution through inverted 32 x 32 diagonal blocks); SPARSE:
- * the sparse Cholesky factor of strom_sdp_factor_info (level-scheduled
- * substitution). Both take the same pivot decisions in the same order and
- * give the same y up to rounding. AUTO: DENSE when every clique group has
- * at most 800 rows and the dense factor takes at most 8 GB, else SPARSE. */
+ * the sparse Cholesky factor of strom_sdp_factor_info (substitution in
+ * blocks of 32 positions). Both take the same pivot decisions in the same
+ * order and give the same y up to rounding. AUTO: DENSE when every clique
+ * group has at most 800 rows and the dense factor takes at most a quarter
+ * of the device's free memory at creation, else SPARSE. */
 enum { STROM_FACTOR_AUTO = 0, STROM_FACTOR_DENSE = 1, STROM_FACTOR_SPARSE = 2 };
 
 /* precision modes of the PSD projection */
@@ -242,6 +243,9 @@ typedef struct {
 int strom_solver_create(const strom_sdp* const* sdps, int32_t count, const strom_options* opt,
                         strom_solver** out);
 void strom_solver_destroy(strom_solver* s);
+/* The factorisation the solver chose (STROM_FACTOR_DENSE or _SPARSE; -1 for
+ * a NULL solver). */
+int32_t strom_solver_factor_kind(const strom_solver* s);
 int32_t strom_solver_count(const strom_solver* s);
 
 /* Recomputes the row reduction and the factorisation of A A^T from the data

@@ -243,6 +243,11 @@ class Solver:
     def __len__(self):
         return lib().strom_solver_count(self.handle)
 
+    @property
+    def factor_kind(self) -> int:
+        """STROM_FACTOR_DENSE or STROM_FACTOR_SPARSE: the y-solve factor in use."""
+        return lib().strom_solver_factor_kind(self.handle)
+
     def factor(self, stream=None):
         """Row reduction + factorisation from device-resident data, fresh state."""
         check(lib().strom_solver_factor(self.handle, stream), "strom_solver_factor")

@@ -343,7 +343,14 @@ void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
   {
     int fk = s->opt.factor;
     const double dense_bytes = 8.0 * (2.0 * (double)fac_acc + (double)coup_acc + (double)dinv_acc);
-    if (fk == STROM_FACTOR_AUTO) fk = (s->max_group <= 800 && dense_bytes <= 8e9) ? STROM_FACTOR_DENSE : STROM_FACTOR_SPARSE;
+    if (fk == STROM_FACTOR_AUTO) {
+      // dense per-clique groups while they are small (their block steps are
+      // shorter than the sparse factor's) and take at most a quarter of the
+      // device's free memory; the sparse factor otherwise
+      size_t free_b = 0, total_b = 0;
+      STROM_CUDA(cudaMemGetInfo(&free_b, &total_b));
+      fk = (s->max_group <= 800 && dense_bytes <= 0.25 * (double)free_b) ? STROM_FACTOR_DENSE : STROM_FACTOR_SPARSE;
+    }
     s->factor_kind = fk;
   }
   const bool dense = s->factor_kind == STROM_FACTOR_DENSE;
@@ -484,6 +491,7 @@ extern "C" int strom_solver_create(const strom_sdp* const* sdps, int32_t count, 
 }
 
 extern "C" void strom_solver_destroy(strom_solver* s) { delete s; }
+extern "C" int32_t strom_solver_factor_kind(const strom_solver* s) { return s ? s->factor_kind : -1; }
 extern "C" int32_t strom_solver_count(const strom_solver* s) { return s ? s->ninst : 0; }
 extern "C" int64_t strom_solver_nsvec_total(const strom_solver* s) { return s ? s->nsvec : 0; }
 extern "C" int64_t strom_solver_m_total(const strom_solver* s) { return s ? s->m : 0; }

@@ -230,19 +230,19 @@ __global__ void __launch_bounds__(BINV_W * 32) sp_blockinv_kernel(SpDev d, const
 //                        subtracts its entries in earlier blocks of its group
 //                        (8 lanes per row, a fixed 3-step sum), and the block
 //                        is solved through the inverse of its diagonal part
-//                        (one thread per output, four partial sums)
+//                        (8 lanes per output, a fixed 3-step sum)
 //  backward (L^T y = w): the same with the columns' entries in the next group
 //                        and in later blocks, and the transposed inverse,
 //                        blocks and groups last to first
 // The entries a step needs do not depend on the solution, so each step loads
-// the next step's first entries (up to 32 of a row), its rows' entry ranges
+// the next step's first entries (up to 64 of a row), its rows' entry ranges
 // two steps ahead, and
 // its block inverse while the current step computes: a step waits on shared
 // memory and on the FP64 pipe, not on global memory. Two barriers a step.
-// entries per lane loaded a step ahead: 4 (32 entries of a row) for up to
-// four right-hand sides per CTA, 2 for eight (registers); the per-lane
+// entries per lane loaded a step ahead: 8 (64 entries of a row) for one or
+// two right-hand sides per CTA, fewer for more (registers); the per-lane
 // order of the entries, and so the arithmetic, is the same for every choice
-template <int R> struct SpPf { static constexpr int value = R <= 4 ? 4 : 2; };
+template <int R> struct SpPf { static constexpr int value = R <= 2 ? 8 : R == 4 ? 4 : 2; };
 constexpr int SP_MAXG = kSpMaxGroups;
 
 // walks the blocks of a pass in order (forward: first to last, backward: last
@@ -282,7 +282,9 @@ __device__ void sp_pass_impl(const SpDev& d, const SpPatDev& P, const SpInstDev*
   const int nt = P.n_tail, G = P.ngroups;
   auto buf = [&](int g, int r) -> double* { return sh + ((size_t)(g & 1) * R + r) * MG; };
   const int q = tid >> 3, l8 = tid & 7;     // gather: row / column q of the block, 8 lanes each
-  const int oj = tid % BS, orr = tid / BS;  // block inverse: output oj of instance orr
+  // block inverse: output ioj, terms 4 ik .. 4 ik + 3 (8 lanes per output,
+  // every warp busy: the FP64 pipe of each of the SM's four partitions)
+  const int ioj = tid >> 3, ik = tid & 7;
   // entries of row / column p inside its group, in earlier blocks: [segb[p], sege[p])
   const int64_t* segb = FWD ? P.fgrp : P.bsplit;
   const int64_t* sege = FWD ? P.fsplit : P.bgrp;
@@ -303,7 +305,7 @@ __device__ void sp_pass_impl(const SpDev& d, const SpPatDev& P, const SpInstDev*
   int64_t cur_e = 0, cur_end = 0, nb_e = 0, nb_end = 0, nn_e = 0, nn_end = 0;
   int32_t pf_j[SP_PF];
   double pf_v[SP_PF][R];
-  double dv[BS];
+  double dv[R][4];
   auto load_range = [&](const BlkIt& it, int64_t& e, int64_t& end) {
     e = 0; end = 0;
     if (q < it.bs) { e = segb[it.b0 + q] + l8; end = sege[it.b0 + q]; }
@@ -320,11 +322,17 @@ __device__ void sp_pass_impl(const SpDev& d, const SpPatDev& P, const SpInstDev*
     }
   };
   auto load_inverse = [&](const BlkIt& it) {
-    if (it.bs == 0 || orr >= R) return;
-    const SpInstDev& I = sI[orr];
-    const double* Db = d.dinvb + ((it.bb < P.tail_blk) ? I.v_tail : I.v_own) + (int64_t)it.bb * (BS * BS);
+    if (it.bs == 0) return;
 #pragma unroll
-    for (int t = 0; t < BS; ++t) dv[t] = FWD ? Db[t * BS + oj] : Db[oj * BS + t];
+    for (int r = 0; r < R; ++r) {
+      const SpInstDev& I = sI[r];
+      const double* Db = d.dinvb + ((it.bb < P.tail_blk) ? I.v_tail : I.v_own) + (int64_t)it.bb * (BS * BS);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int t = 4 * ik + i;
+        dv[r][i] = FWD ? Db[t * BS + ioj] : Db[ioj * BS + t];
+      }
+    }
   };
   auto flush = [&](int g, int a, int b) {
     for (int t = tid; t < R * (b - a); t += SOLVE_T) {
@@ -427,14 +435,21 @@ __device__ void sp_pass_impl(const SpDev& d, const SpPatDev& P, const SpInstDev*
     cur_e = nb_e; cur_end = nb_end;
     nb_e = nn_e; nb_end = nn_end;
     __syncthreads();
-    // the block through the inverse of its diagonal part
-    if (orr < R && oj < bs) {
-      // four partial sums (t mod 4), then (s0 + s1) + (s2 + s3): a short
-      // dependency chain, the same order for every tile size
-      double o4[4] = {0.0, 0.0, 0.0, 0.0};
+    // the block through the inverse of its diagonal part: each output as 8
+    // partial sums of 4 terms, added by a fixed shuffle tree (the same
+    // arithmetic for every tile size)
 #pragma unroll
-      for (int t = 0; t < BS; ++t) o4[t & 3] += (t < bs) ? dv[t] * tb[orr][t] : 0.0;
-      buf(g, orr)[b0 - a + oj] = (o4[0] + o4[1]) + (o4[2] + o4[3]);
+    for (int r = 0; r < R; ++r) {
+      double c = 0.0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int t = 4 * ik + i;
+        c += (t < bs) ? dv[r][i] * tb[r][t] : 0.0;
+      }
+      c += __shfl_xor_sync(0xffffffffu, c, 1);
+      c += __shfl_xor_sync(0xffffffffu, c, 2);
+      c += __shfl_xor_sync(0xffffffffu, c, 4);
+      if (ik == 0 && ioj < bs) buf(g, r)[b0 - a + ioj] = c;
     }
     load_inverse(it1);
     __syncthreads();
@@ -448,7 +463,7 @@ __device__ void sp_pass_impl(const SpDev& d, const SpPatDev& P, const SpInstDev*
 
 template <int R>
 __global__ void __launch_bounds__(SOLVE_T) sp_solve_kernel(SpDev d, double* __restrict__ yout) {
-  static_assert(kSpBlock * R <= SOLVE_T, "one thread per (output, instance) of a block inverse");
+  static_assert(R >= 1 && R <= 8, "tiles of 1 to 8 instances");
   extern __shared__ double sh[];
   const int i0 = blockIdx.x * R;
   const int tid = threadIdx.x;

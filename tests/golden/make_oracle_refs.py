@@ -15,7 +15,11 @@ Sets (instance i of a set is workloads.problem_batch(kind, ...)[i]):
               (N ~ U{20..100}) with the shortest horizons
   mixed       requests of the seeded serving stream (workloads.mixed_request,
               keyed by request index): the first 16 pendulum requests and the
-              first 6 cart-pole requests
+              first 6 cart-pole requests, solved at the served accuracy
+              (KKT 1e-6, at most 20,000 iterations, as the server): at these
+              horizons Algorithm 1 can stall far above 1e-8 (the pendulum at
+              N = 31 and 52 stood at eta_d ~ 4e-4 and 8e-4 after 60,000
+              iterations)
 
 Usage: python tests/golden/make_oracle_refs.py SET [SET ...] [--workers K]
 Existing entries are kept; only missing ones are computed. Single-threaded BLAS per worker.
@@ -74,9 +78,11 @@ def solve_one(args):
     p = dict(instances(kind))[i]
     t0 = time.time()
     red = OA.reduce(OR.relax(p))
-    res = OA.solve(red, OA.Options(tol=TOL, maxiter=MAXITER))
+    tol, maxiter = (1e-6, 20000) if kind == "mixed" else (TOL, MAXITER)
+    res = OA.solve(red, OA.Options(tol=tol, maxiter=maxiter))
     c = OC.certify(p, red, res.X, res.y)
-    return {"kind": kind, "index": i, "N": p.N, "iterations": res.iters, "converged": bool(res.converged),
+    return {"kind": kind, "index": i, "N": p.N, "robot": p.name, "tol": tol, "maxiter": maxiter,
+            "iterations": res.iters, "converged": bool(res.converged),
             "pobj": res.pobj, "dobj": res.dobj, "eta": [res.eta_p, res.eta_d, res.eta_g],
             "m_kept": int(red.keep.sum()), "max_ratio": c.max_ratio, "feasible": bool(c.feasible),
             "rank_one": bool(c.rank_one), "certified": bool(c.certified), "lower_bound": c.lower_bound,
