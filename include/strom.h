@@ -209,7 +209,10 @@ typedef struct {
   int32_t precision;         /* STROM_PREC_* */
   double polish_eta;         /* MIXED: switch to the FP64 eigensolver once eta <= polish_eta; an
                                 instance meeting tol in FP32 switches too, and it retires only
-                                on an FP64 iterate with eta <= tol */
+                                on an FP64 iterate with eta <= tol. It also switches when its
+                                FP32 phase stalls: at eta <= 1e-4, less than 5 % progress over
+                                200 iterations (the FP32 eigensolver's rounding can hold eta
+                                above polish_eta) */
   int32_t check_every;       /* host checks for completion every this many iterations */
   double time_budget_s;      /* strom_solve only: wall-clock budget in seconds, checked every
                                 check_every iterations; when spent, strom_solve returns

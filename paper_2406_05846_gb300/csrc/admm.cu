@@ -109,6 +109,11 @@ __global__ void __launch_bounds__(CT) primal_res_kernel(AdmmDev d, const double*
   }
 }
 
+// mixed precision: stall test of the FP32 phase (see finalize_kernel)
+constexpr int kStallWindow = 200;
+constexpr double kStallEta = 1e-4;
+constexpr double kStallRatio = 0.95;
+
 // per instance: eta_p, eta_d, eta_g (eq. kkt-residual), stop test, sigma rule
 __global__ void __launch_bounds__(1024) finalize_kernel(AdmmDev d, AdmmParams prm) {
   __shared__ int cnt[32];
@@ -157,8 +162,21 @@ __global__ void __launch_bounds__(1024) finalize_kernel(AdmmDev d, AdmmParams pr
       d.inst_flag[i] = 3;
       continue;
     }
-    if (prm.precision == STROM_PREC_MIXED && d.inst_prec[i] == STROM_PREC_FP32 && eta <= prm.polish_eta)
-      d.inst_prec[i] = STROM_PREC_FP64;
+    if (prm.precision == STROM_PREC_MIXED && d.inst_prec[i] == STROM_PREC_FP32) {
+      if (eta <= prm.polish_eta) {
+        d.inst_prec[i] = STROM_PREC_FP64;
+      } else if (it % kStallWindow == 0) {
+        // the FP32 eigensolver's rounding (about 1e-6 relative) can stall
+        // the residuals above polish_eta: below kStallEta, an FP32 phase
+        // that gains less than 5 % over a window switches to FP64 too. The
+        // checkpoint of the previous window counts only if it is this
+        // run's (it_ref == it - window), so a reset needs no clearing.
+        if (d.it_ref[i] == it - kStallWindow && eta <= kStallEta && eta > kStallRatio * d.eta_ref[i])
+          d.inst_prec[i] = STROM_PREC_FP64;
+        d.eta_ref[i] = eta;
+        d.it_ref[i] = it;
+      }
+    }
     if (prm.sigma_every > 0 && it % prm.sigma_every == 0) {
       const double epg = fmax(ep, eg);
       double sg = d.sigma[i];

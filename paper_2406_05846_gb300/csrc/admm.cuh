@@ -39,6 +39,8 @@ struct AdmmDev {
   uint8_t* inst_prec;
   int32_t* iters;
   int32_t* iters64;     // consecutive iterations projected with the FP64 eigensolver
+  double* eta_ref;      // mixed precision: eta at the last stall checkpoint of the FP32 phase
+  int32_t* it_ref;      // and its iteration (-1 at allocation)
   double* stats;        // [ninst * 8]: eta_p, eta_d, eta_g, pobj, dobj
   double* part_svec;
   double* part_rows;

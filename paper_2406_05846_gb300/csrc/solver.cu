@@ -380,6 +380,10 @@ void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
   s->inst_prec.alloc(count);
   s->iters.alloc(count);
   s->iters64.alloc(count);
+  s->eta_ref.alloc(count);
+  s->it_ref.alloc(count);
+  STROM_CUDA(cudaMemsetAsync(s->it_ref.p, 0xFF, sizeof(int32_t) * count, st));  // -1: no checkpoint yet
+  STROM_CUDA(cudaMemsetAsync(s->eta_ref.p, 0, sizeof(double) * count, st));
   s->n_active.alloc(1);
   s->blk_act32.alloc(s->nblk);
   s->blk_act64.alloc(s->nblk);
@@ -424,6 +428,7 @@ void solver_setup(strom_solver* s, const strom_sdp* const* sdps, int count) {
   ad.b = s->b.p; ad.C = s->C.p; ad.keep = s->keep.p; ad.norm_b = s->norm_b.p; ad.norm_C = s->norm_C.p;
   ad.X = s->X.p; ad.S = s->S.p; ad.sigma = s->sigma.p; ad.inst_active = s->inst_active.p;
   ad.inst_flag = s->inst_flag.p; ad.inst_prec = s->inst_prec.p; ad.iters = s->iters.p; ad.iters64 = s->iters64.p; ad.stats = s->stats.p;
+  ad.eta_ref = s->eta_ref.p; ad.it_ref = s->it_ref.p;
   ad.part_svec = s->part_svec.p; ad.part_rows = s->part_rows.p; ad.n_active = s->n_active.p;
   ad.blk_inst = s->blk_inst.p; ad.blk_act32 = s->blk_act32.p; ad.blk_act64 = s->blk_act64.p;
   ad.blk_inv_sigma = s->blk_inv_sigma.p;

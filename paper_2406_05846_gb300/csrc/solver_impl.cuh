@@ -80,6 +80,8 @@ struct strom_solver {
   DevBuf<float> vstore;     // FP32 eigenvectors of every block, kept for the warm start
   DevBuf<double> vstore64;  // FP64 eigenvectors (polish / FP64 mode)
   DevBuf<int32_t> iters64;  // consecutive FP64 iterations of each instance
+  DevBuf<double> eta_ref;   // stall checkpoints of the mixed-precision FP32 phase
+  DevBuf<int32_t> it_ref;
   DevBuf<int32_t> col, atrow, row_inst, star_ptr, star_inst, inst_grp, coup_n, grp_len, blk_n, blk_list, blk_inst;
   DevBuf<int32_t> inst_svec_chunk, inst_row_chunk, iters, n_active;
   DevBuf<double> val, atval, b, C, omega, inv_rep_s, star_c, star_d, star_inv_s2, fac, lt, coup, diag0;
