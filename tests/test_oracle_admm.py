@@ -234,3 +234,39 @@ def test_paper_pendulum_relaxation_matches_brute_force():
     assert res.pobj <= pbf + 1e-6 * (1 + abs(pbf))
     assert abs(res.pobj - pbf) <= 1e-6 * (1 + abs(pbf))
     assert cert.lower_bound <= pbf + 1e-9
+
+
+def test_sigma_rule_recovers_from_a_badly_scaled_start(monkeypatch):
+    """The sigma rule (reading 7: balance eta_d against max(eta_p, eta_g))
+    pinned by its effect, not its formula: on the trace-constrained SDP with
+    a closed-form optimum, with the cost scaled by 1e-3, 1 or 1e3 and
+    sigma0 in {1e-3, 10, 1e3}, Algorithm 1 reaches the closed-form optimum
+    within 3,000 iterations every time; the same rule with its two branches
+    swapped (a plausible sign mistake, planted here on the CPU) does not."""
+    rng = np.random.default_rng(21)
+    mats = []
+    for n in (3, 5, 8):
+        G = rng.standard_normal((n, n))
+        mats.append(0.5 * (G + G.T))
+    for scale in (1e-3, 1.0, 1e3):
+        red = _trace_sdp([scale * M for M in mats])
+        want = scale * sum(np.linalg.eigvalsh(M)[0] for M in mats)
+        for s0 in (1e-3, 10.0, 1e3):
+            res = O.solve(red, O.Options(tol=1e-8, maxiter=3000, sigma0=s0))
+            assert res.converged, (scale, s0, res.iters)
+            assert abs(res.pobj - want) <= 1e-6 * (1 + abs(want)), (scale, s0)
+
+    def swapped(sigma, eta_p, eta_d, eta_g, opt):
+        eta_pg = max(eta_p, eta_g)
+        if eta_pg > opt.sigma_ratio * eta_d:
+            sigma *= opt.sigma_factor
+        elif eta_d > opt.sigma_ratio * eta_pg:
+            sigma /= opt.sigma_factor
+        return min(max(sigma, opt.sigma_min), opt.sigma_max)
+
+    monkeypatch.setattr(O, "sigma_update", swapped)
+    fails = 0
+    for scale, s0 in ((1.0, 10.0), (1e3, 10.0), (1e-3, 1e-3)):
+        red = _trace_sdp([scale * M for M in mats])
+        fails += not O.solve(red, O.Options(tol=1e-8, maxiter=3000, sigma0=s0)).converged
+    assert fails == 3
