@@ -116,8 +116,8 @@ def test_served_requests_match_oracle():
 
 def test_cartpole_batch_of_8_matches_oracle():
     """Cart-pole N = 50, the seeded instances that have an oracle reference
-    (of the first 8), one batched solver in mixed precision with the sparse
-    factor of the y-solve and a shared tail. Its relaxation is not tight
+    (of the first 8), one batched solver with the sparse factor of the
+    y-solve and a shared tail, FP64 eigensolver. Its relaxation is not tight
     (lambda_2 / lambda_1 about 0.7: not certified, like the oracle's), and
     at KKT 1e-6 the objective is still about 1e-5 (relative) from the
     optimum, so this test solves to KKT 1e-7 to hold the 1e-6 objective bar."""
@@ -131,8 +131,8 @@ def test_cartpole_batch_of_8_matches_oracle():
     refs = [have[str(i)] for i in idx]
     probs = wl.problem_batch("cartpole", 8, N=50)
     P = [S.Problem(probs[i]) for i in idx]
-    solver = S.Solver([q.relax() for q in P], tol=1e-7, maxiter=40000, precision=S.STROM_PREC_MIXED,
-                      polish_eta=1e-6, check_every=100, factor=S.STROM_FACTOR_SPARSE)
+    solver = S.Solver([q.relax() for q in P], tol=1e-7, maxiter=12000, precision=S.STROM_PREC_FP64,
+                      check_every=100, factor=S.STROM_FACTOR_SPARSE)
     assert solver.solve() == S.STROM_OK
     certs = solver.certify_batch(P)
     for k, i in enumerate(idx):
