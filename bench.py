@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--horizon-batch", type=int, default=0,
                     help="cartpole / rigid workloads: horizon (0 = 50 / N ~ U{20..100})")
     ap.add_argument("--check", type=int, default=100, help="cartpole / rigid workloads: iterations between checks")
+    ap.add_argument("--eig-reorth", type=int, default=0,
+                    help="cartpole / rigid workloads: re-orthonormalise the FP32 warm-start eigenvectors (0 / 1)")
     ap.add_argument("--workload", default="served", choices=["served", "psd", "warm", "poisson", "cartpole", "rigid",
                                                            "mixed"],
                     help="served: certified solves/s (default); psd: the 4096-block PSD-projection microbench; "
@@ -690,7 +692,7 @@ def run_batch(a):
     P, sdps = relax_all(S, probs)
     t_relax = time.perf_counter() - t0
     opts = dict(tol=1e-6, maxiter=a.maxiter, precision=S.STROM_PREC_MIXED, polish_eta=a.polish_eta,
-                check_every=a.check, factor=S.STROM_FACTOR_SPARSE)
+                check_every=a.check, factor=S.STROM_FACTOR_SPARSE, eig_reorth=a.eig_reorth)
     t0 = time.perf_counter()
     sv = S.Solver(sdps, **opts)
     torch.cuda.synchronize()

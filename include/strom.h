@@ -226,6 +226,10 @@ typedef struct {
                                 cliques 2..N is computed once and shared (cliques are eliminated
                                 N..1, so only the first clique's factor differs) */
   int32_t factor;            /* STROM_FACTOR_*: how A A^T is factorised for the y-solve */
+  int32_t eig_reorth;        /* 1: a warm-started FP32 eigensolve of a block of 41..80 rows first
+                                takes one Newton-Schulz step, V <- (3 V - V V^T V) / 2, towards
+                                orthonormal stored eigenvectors (they drift in FP32 from one
+                                iteration to the next); 0 (default): none */
 } strom_options;
 
 void strom_options_default(strom_options* o);

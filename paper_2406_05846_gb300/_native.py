@@ -49,7 +49,7 @@ class strom_options(C.Structure):
                 ("sigma_min", C.c_double), ("sigma_max", C.c_double), ("rank_tol", C.c_double),
                 ("precision", C.c_int32), ("polish_eta", C.c_double), ("check_every", C.c_int32),
                 ("time_budget_s", C.c_double), ("eig_warm_period", C.c_int32),
-                ("share_tail", C.c_int32), ("factor", C.c_int32)]
+                ("share_tail", C.c_int32), ("factor", C.c_int32), ("eig_reorth", C.c_int32)]
 
 
 class strom_result(C.Structure):

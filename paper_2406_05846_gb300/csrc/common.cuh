@@ -141,6 +141,7 @@ struct PsdArgs {
   const int32_t* blk_inst;
   const int32_t* inst_iter;
   int warm_period;
+  int reorth;   // 1: re-orthonormalise the stored FP32 eigenvectors of blocks of 41..80 rows (warm starts)
   // the same for the FP64 eigensolver (the polish): eigenvectors in vstore64,
   // inst_iter64 counts an instance's consecutive FP64 iterations
   double* vstore64;

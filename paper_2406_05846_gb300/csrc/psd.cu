@@ -153,6 +153,60 @@ __global__ void __launch_bounds__(NT) jacobi_psd_kernel(PsdArgs a, int list_star
     }
   }
   fro = block_sum<NT>(fro, red);   // contains a barrier
+  if constexpr (SM::WARM && sizeof(T) == 4 && NP > 40) {
+    if (warm && a.reorth) {
+      // One Newton-Schulz step towards orthonormal rows,
+      // V <- (3 V - (V V^T) V) / 2. The stored FP32 eigenvectors drift from
+      // orthogonality over the iterations between cold restarts; on the
+      // cart-pole's 78 x 78 blocks that drift leaves the projection an error
+      // floor near 1e-5, which the sigma rule answers by shrinking sigma
+      // until the iteration diverges. G = V V^T goes to Tm (free until the
+      // warm start below), the new rows to registers, then back to V.
+      const int h2 = np / 2, nt2 = h2 * h2;
+      for (int it = tid; it < nt2; it += NT) {
+        const int i0 = 2 * (it / h2), j0 = 2 * (it % h2);
+        T g00 = 0, g01 = 0, g10 = 0, g11 = 0;
+        for (int k = 0; k < np; ++k) {
+          const T a0 = V[i0 * LDV + k], a1 = V[(i0 + 1) * LDV + k];
+          const T b0 = V[j0 * LDV + k], b1 = V[(j0 + 1) * LDV + k];
+          g00 += a0 * b0; g01 += a0 * b1; g10 += a1 * b0; g11 += a1 * b1;
+        }
+        Tm[i0 * LD + j0] = g00; Tm[i0 * LD + j0 + 1] = g01;
+        Tm[(i0 + 1) * LD + j0] = g10; Tm[(i0 + 1) * LD + j0 + 1] = g11;
+      }
+      __syncthreads();
+      constexpr int MAXT = ((NP / 2) * (NP / 2) + NT - 1) / NT;
+      T nv[MAXT][4];
+#pragma unroll
+      for (int m = 0; m < MAXT; ++m) {
+        const int it = tid + m * NT;
+        if (it < nt2) {
+          const int i0 = 2 * (it / h2), c0 = 2 * (it % h2);
+          T s00 = 0, s01 = 0, s10 = 0, s11 = 0;
+          for (int k = 0; k < np; ++k) {
+            const T g0 = Tm[i0 * LD + k], g1 = Tm[(i0 + 1) * LD + k];
+            const T v0 = V[k * LDV + c0], v1 = V[k * LDV + c0 + 1];
+            s00 += g0 * v0; s01 += g0 * v1; s10 += g1 * v0; s11 += g1 * v1;
+          }
+          nv[m][0] = T(1.5) * V[i0 * LDV + c0] - T(0.5) * s00;
+          nv[m][1] = T(1.5) * V[i0 * LDV + c0 + 1] - T(0.5) * s01;
+          nv[m][2] = T(1.5) * V[(i0 + 1) * LDV + c0] - T(0.5) * s10;
+          nv[m][3] = T(1.5) * V[(i0 + 1) * LDV + c0 + 1] - T(0.5) * s11;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int m = 0; m < MAXT; ++m) {
+        const int it = tid + m * NT;
+        if (it < nt2) {
+          const int i0 = 2 * (it / h2), c0 = 2 * (it % h2);
+          V[i0 * LDV + c0] = nv[m][0]; V[i0 * LDV + c0 + 1] = nv[m][1];
+          V[(i0 + 1) * LDV + c0] = nv[m][2]; V[(i0 + 1) * LDV + c0 + 1] = nv[m][3];
+        }
+      }
+      __syncthreads();
+    }
+  }
   if constexpr (SM::WARM) {
     if (warm) {
       // B = V X V^T in the stored eigenbasis (V^T rows are the eigenvectors):

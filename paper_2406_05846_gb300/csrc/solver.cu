@@ -70,6 +70,7 @@ PsdArgs psd_args(strom_solver* s, const double* in, double* out, const uint8_t* 
     a.inst_iter = s->iters.p;
     a.inst_iter64 = s->iters64.p;
     a.warm_period = s->opt.eig_warm_period;
+    a.reorth = s->opt.eig_reorth;
   }
   a.Xb = in;
   a.out = out;
@@ -463,6 +464,7 @@ extern "C" void strom_options_default(strom_options* o) {
   o->check_every = 50;
   o->time_budget_s = 0.0;
   o->eig_warm_period = 20;
+  o->eig_reorth = 0;
   o->share_tail = 1;
   o->factor = STROM_FACTOR_AUTO;
 }
@@ -478,7 +480,7 @@ extern "C" int strom_solver_create(const strom_sdp* const* sdps, int32_t count, 
     else strom_options_default(&s->opt);
     const auto& o = s->opt;
     if (!(o.tol > 0) || o.maxiter < 1 || !(o.sigma0 > 0) || !(o.tau > 0 && o.tau < 2) || !(o.rank_tol > 0) ||
-        o.precision < 0 || o.precision > 2 || o.check_every < 1 || o.eig_warm_period < 0 || o.factor < 0 ||
+        o.precision < 0 || o.precision > 2 || o.check_every < 1 || o.eig_warm_period < 0 || o.eig_reorth < 0 || o.eig_reorth > 1 || o.factor < 0 ||
         o.factor > 2)
       throw StatusError(STROM_ERR_INVALID, "strom_solver_create: invalid options");
     // the PSD kernels keep a block of up to 160 rows in shared memory

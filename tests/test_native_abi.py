@@ -256,3 +256,34 @@ def test_plain_c_client(S, tmp_path):
     assert lines["warm_select"] == "0 k 3 idx 0 2 1 wt 0.500000 0.300000 0.200000"
     assert lines["rank_test"] == "0 rank 1 flat 1 zbar 0.500000 -0.250000 0.750000"
     assert lines["solver_create"] in ("ok", "cuda-unavailable")
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes structures of the binding have the size and field offsets
+    that a C compiler gives the structures of strom.h."""
+    import shutil
+    import subprocess
+    from paper_2406_05846_gb300 import _native as N
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"strom_options": N.strom_options, "strom_result": N.strom_result,
+               "strom_certificate": N.strom_certificate, "strom_tune_report": N.strom_tune_report,
+               "strom_server_class": N.strom_server_class, "strom_factor_info": N.strom_factor_info}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "strom.h"', 'int main(void) {']
+    for name, cls in structs.items():
+        lines.append('  printf("%s %%zu\\n", sizeof(%s));' % (name, name))
+        for fname, _ in cls._fields_:
+            lines.append('  printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, fname, name, fname))
+    lines.append('  return 0;\n}')
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = str(tmp_path / "layout")
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", exe], check=True,
+                   capture_output=True)
+    got = dict(line.split() for line in subprocess.run([exe], capture_output=True, text=True,
+                                                        check=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert int(got["%s.%s" % (name, fname)]) == getattr(cls, fname).offset, (name, fname)
