@@ -523,6 +523,14 @@ int strom_solver_offsets(const strom_solver* s, int32_t i, int64_t* svec_off, in
 int strom_kernel_A(const strom_solver* s, const double* x_dev, double* Ax_dev, void* stream);
 /* x_dev = A^* y = sum_l y_l A_l over all rows (Sec. 3). */
 int strom_kernel_At(const strom_solver* s, const double* y_dev, double* x_dev, void* stream);
+/* The same products for an operator given by raw device arrays: y_dev =
+ * M x_dev for a CSR matrix M of nrows rows (rowptr_dev: int64 [nrows + 1],
+ * col_dev: int32 column indices, val_dev: FP64 values, all on the device,
+ * borrowed for the call). With A's rows (strom_sdp_export) it is A(X); with
+ * the CSR of A^T it is A^*(y) (Sec. 3). x_dev and y_dev may not alias;
+ * nrows = 0 does nothing. Asynchronous on `stream`. Errors: INVALID. */
+int strom_kernel_spmv_csr(const int64_t* rowptr_dev, const int32_t* col_dev, const double* val_dev,
+                          int64_t nrows, const double* x_dev, double* y_dev, void* stream);
 /* y_dev = (A_K A_K^T)^{-1} r_K on the kept rows K, zero on dropped rows
  * (eq. solve-y1 / solve-y2). r_dev entries of dropped rows are ignored. */
 int strom_kernel_solve(const strom_solver* s, const double* r_dev, double* y_dev, void* stream);

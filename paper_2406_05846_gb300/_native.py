@@ -135,6 +135,7 @@ SIGNATURES = {
     "strom_solver_tune": (C.c_int, [P, C.c_int32, P, C.POINTER(strom_tune_report)]),
     "strom_batch_create": (C.c_int, [P, C.c_int32, C.POINTER(strom_options), C.POINTER(P)]),
     "strom_solver_factor_kind": (C.c_int32, [P]),
+    "strom_kernel_spmv_csr": (C.c_int, [P, P, P, C.c_int64, P, P, P]),
     "strom_batch_slot_bytes": (C.c_int, [P, C.POINTER(strom_options), PI64, PI64, PI64]),
     "strom_server_create": (C.c_int, [C.c_int64, C.c_int32, C.POINTER(strom_options), C.POINTER(P)]),
     "strom_server_destroy": (None, [P]),

@@ -630,6 +630,14 @@ def _check_blocks(off, n):
         raise ValueError("blk_off has %d entries but blk_n has %d" % (off.size, n.size))
 
 
+def kernel_spmv_csr(rowptr_ptr, col_ptr, val_ptr, nrows, x_ptr, y_ptr, stream=None):
+    """strom_kernel_spmv_csr: y = M x for a CSR matrix in device memory (int64
+    row pointers, int32 columns, FP64 values): A(X) with A's rows, A^*(y)
+    with A^T's."""
+    check(lib().strom_kernel_spmv_csr(rowptr_ptr, col_ptr, val_ptr, int(nrows), x_ptr, y_ptr, stream),
+          "strom_kernel_spmv_csr")
+
+
 def kernel_psd_project(xb_ptr, blk_off, blk_n, precision, out_ptr, stream=None):
     off = np.ascontiguousarray(blk_off, np.int64).ravel()
     n = np.ascontiguousarray(blk_n, np.int32).ravel()

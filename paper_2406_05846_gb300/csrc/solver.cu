@@ -937,6 +937,16 @@ extern "C" int strom_kernel_A(const strom_solver* s, const double* x_dev, double
   });
 }
 
+extern "C" int strom_kernel_spmv_csr(const int64_t* rowptr_dev, const int32_t* col_dev, const double* val_dev,
+                                     int64_t nrows, const double* x_dev, double* y_dev, void* stream) {
+  return guard([&] {
+    if (nrows < 0 || (nrows > 0 && (!rowptr_dev || !col_dev || !val_dev || !x_dev || !y_dev || x_dev == y_dev)))
+      throw StatusError(STROM_ERR_INVALID, "strom_kernel_spmv_csr: bad arguments");
+    csr_spmv(rowptr_dev, col_dev, val_dev, nrows, x_dev, y_dev, (cudaStream_t)stream);
+    return STROM_OK;
+  });
+}
+
 extern "C" int strom_kernel_At(const strom_solver* s, const double* y_dev, double* x_dev, void* stream) {
   return guard([&] {
     if (!s || !x_dev || !y_dev) throw StatusError(STROM_ERR_INVALID, "strom_kernel_At: bad arguments");

@@ -135,3 +135,22 @@ def test_multi_rhs_solve_matches_single(tile, monkeypatch):
         so, ro = one.offsets(i)
         want = OA.YSolver(red.A)(r[ro:ro + red.sdp.m][red.keep])
         assert_close(b[ro:ro + red.sdp.m][red.keep], want, 1e-10, what=("y", i))
+
+
+def test_raw_csr_products_match_oracle():
+    """strom_kernel_spmv_csr on the oracle's A and A^T given as raw device
+    arrays (int64 row pointers, int32 columns, FP64 values): A(X) and A^*(y)
+    against SciPy's products of the same matrices, entry by entry."""
+    S = lib()
+    o = OR.relax(wl.pendulum_problem(N=6, theta0=0.08))
+    rng = np.random.default_rng(11)
+    for M in (o.A.tocsr(), o.A.T.tocsr()):
+        M.sort_indices()
+        x = rng.standard_normal(M.shape[1])
+        rp = torch.tensor(M.indptr.astype(np.int64), device="cuda:0")
+        ci = torch.tensor(M.indices.astype(np.int32), device="cuda:0")
+        va = torch.tensor(M.data.astype(np.float64), device="cuda:0")
+        xd = dev(x)
+        yd = torch.zeros(M.shape[0], dtype=torch.float64, device="cuda:0")
+        S.kernel_spmv_csr(rp.data_ptr(), ci.data_ptr(), va.data_ptr(), M.shape[0], xd.data_ptr(), yd.data_ptr())
+        assert_close(host(yd), M @ x, 1e-13, what=M.shape)

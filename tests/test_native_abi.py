@@ -287,3 +287,13 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(got[name]) == ctypes.sizeof(cls), name
         for fname, _ in cls._fields_:
             assert int(got["%s.%s" % (name, fname)]) == getattr(cls, fname).offset, (name, fname)
+
+
+def test_raw_csr_product_argument_checks(S):
+    """strom_kernel_spmv_csr refuses a negative row count and missing
+    pointers before touching the device, and does nothing for zero rows."""
+    L = S.lib()
+    assert L.strom_kernel_spmv_csr(None, None, None, -1, None, None, None) == -1
+    assert b"bad arguments" in L.strom_last_error()
+    assert L.strom_kernel_spmv_csr(None, None, None, 3, None, None, None) == -1
+    assert L.strom_kernel_spmv_csr(None, None, None, 0, None, None, None) == 0
