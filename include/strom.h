@@ -424,7 +424,9 @@ int strom_batch_poll(strom_batch* b, uint64_t ticket, strom_result* r, strom_cer
  * runs every batch with work for `iters` iterations, each from its own host
  * thread and stream, so different structures overlap on the device; each
  * request's arithmetic is the same as solving it alone. Inputs are copied at
- * submit. Latency counts the wait for a batch. The paper has no
+ * submit. Latency counts the wait for a batch. A request whose structure
+ * needs more than the whole budget for one slot finishes at the next step
+ * with result status STROM_ERR_OOM. The paper has no
  * counterpart (its nearest use is the warm-started MPC loop of Sec. 5).
  * Errors: strom_server_create returns OOM (allocating nothing) when
  * budget_bytes exceeds the device's free memory.

@@ -211,6 +211,21 @@ void provision(strom_server* S, int c) {
     k.sized = true;
   }
   const int64_t fixed = k.base + k.transient;
+  if (fixed + k.per > S->budget) {
+    // not one slot of this structure fits the whole budget: its requests
+    // finish at once with STROM_ERR_OOM instead of waiting forever
+    const double t = now_s();
+    for (Waiting& w : k.waiting) {
+      Finished f;
+      f.r.status = STROM_ERR_OOM;
+      f.latency = t - w.t_submit;
+      S->done[w.ticket] = f;
+      S->waiting_cls.erase(w.ticket);
+      free_waiting(w);
+    }
+    k.waiting.clear();
+    return;
+  }
   auto fits = [&]() { return S->budget - S->used - fixed >= k.per; };
   if (!fits()) {
     for (size_t e = 0; e < S->cls.size() && !fits(); ++e) {
