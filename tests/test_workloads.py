@@ -56,3 +56,32 @@ def test_pendulum_batch_recipe():
         rng = np.random.default_rng(np.random.PCG64(BASE_SEED + i))
         assert th[i] == float(rng.uniform(-0.2, 0.2))
     assert all(p.N == 4 and p.nv == 7 for p in batch)
+
+
+def test_serving_stream_recipe():
+    """Config 5's stream: robots in the configured shares (50 / 30 / 20 %),
+    horizons uniform over each robot's range, request j reproducible from
+    its index alone; Poisson arrivals with the configured rate."""
+    import numpy as np
+    counts = {"pendulum": 0, "cartpole": 0, "rigid_body": 0}
+    ranges = {k: rng for k, _, rng in wl.SERVING_MIX}
+    seen = {k: set() for k in counts}
+    n = 1500
+    for j in range(n):
+        kind, p = wl.mixed_request(j)
+        counts[kind] += 1
+        lo, hi = ranges[kind]
+        assert lo <= p.N <= hi
+        seen[kind].add(p.N)
+    for kind, share, _ in wl.SERVING_MIX:
+        assert abs(counts[kind] / n - share) < 0.04, (kind, counts)
+    # every horizon of the pendulum's range appears (uniform over 51 values)
+    assert seen["pendulum"] == set(range(10, 61))
+    k0, p0 = wl.mixed_request(7)
+    k1, p1 = wl.mixed_request(7)
+    assert k0 == k1 and p0.N == p1.N and p0.meta == p1.meta
+    t = wl.poisson_arrivals(40.0, 100.0)
+    assert np.all(np.diff(t) > 0) and t[-1] < 100.0
+    assert abs(len(t) - 4000) < 4 * np.sqrt(4000)
+    gaps = np.diff(t)
+    assert abs(gaps.mean() - 1 / 40.0) < 0.05 / 40.0
