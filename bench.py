@@ -978,6 +978,17 @@ def run_poisson(a):
     print(json.dumps(line))
 
 
+def serving_case(j, kind, converged, certified, pobj, ref):
+    """One sampled served request against the oracle's solve of it at the
+    served accuracy (KKT 1e-6, the same iteration limit): it passes when
+    both reach the same outcome, converged with the same verdict or both
+    stopped at the iteration limit."""
+    return {"request": j, "kind": kind, "converged": converged, "oracle_converged": ref["converged"],
+            "rel_obj": abs(pobj - ref["pobj"]) / (1 + abs(ref["pobj"])),
+            "certified": certified, "oracle_certified": ref["certified"],
+            "pass": converged == ref["converged"] and (not converged or certified == ref["certified"])}
+
+
 def run_mixed(a):
     """Serving the mixed stream (50% pendulum N ~ U{10..60}, 30% cart-pole
     N ~ U{20..80}, 20% planar rigid body N ~ U{20..100}; seeded) arriving as a
@@ -1053,21 +1064,13 @@ def run_mixed(a):
     ok_all = [k for k in res if res[k][0][0].status == S.STROM_OK]
     lat = np.array([res[k][1] for k in ok_all] or [np.nan])
     parity = []
-    # the sample's references are the oracle at the served accuracy (KKT
-    # 1e-6, the same iteration limit): a request passes when the GPU and the
-    # oracle reach the same outcome (both converged with the same verdict,
-    # or both stopped at the iteration limit)
     for k, (j, _, kind, _) in enumerate(reqs):
         ref = refs.get(str(j))
         if ref is None or k not in res:
             continue
         r, c = res[k][0][0], res[k][0][1]
-        conv = r.status == S.STROM_OK
-        cert = bool(c is not None and c.certified)
-        parity.append({"request": j, "kind": kind, "converged": conv, "oracle_converged": ref["converged"],
-                       "rel_obj": abs(r.pobj - ref["pobj"]) / (1 + abs(ref["pobj"])),
-                       "certified": cert, "oracle_certified": ref["certified"],
-                       "pass": conv == ref["converged"] and (not conv or cert == ref["certified"])})
+        parity.append(serving_case(j, kind, r.status == S.STROM_OK, bool(c is not None and c.certified), r.pobj,
+                                   ref))
     line = {"metric": "served mixed requests under Poisson arrivals: solves/s, latency (arrival to result)",
             "value": len(ok_all) / span, "unit": "solves/s", "n_gpus": 1, "steps": 1, "warmup": 0,
             "higher_is_better": True, "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
